@@ -1,0 +1,172 @@
+/*
+ * hdfilter.h -- C ABI of the GB300 (sm_103a) fast high-dimensional bilateral /
+ * nonlocal-means filter of Nair & Chaudhury, "Fast High-Dimensional Bilateral
+ * and Nonlocal Means Filtering" (IEEE TIP; arXiv 1811.02363).
+ *
+ * What is computed (paper notation):
+ *   f : Omega -> R^n      image, n channels          (Eq. (1))
+ *   p : Omega -> R^rho    guide, rho dimensions      (Eq. (1))
+ *   omega(j) = exp(-|j|^2 / 2 sigma_s^2) on W = [-S, S]^2      (Sec. III)
+ *   phi(x)   = exp(-|x|^2 / 2 sigma_r^2)                         (Sec. III)
+ *   Brute force:  g(i) = sum_j omega(j) phi(p(i-j)-p(i)) f(i-j) / eta(i)
+ *                                                      (Eq. (1)-(2))
+ *   Fast filter (Algorithm 1): centres mu_k from bisecting K-means of
+ *   {p(i)} (Sec. II-C); A_kl = phi(mu_k - mu_l), b_k(i) = phi(mu_k - p(i))
+ *   (Eq. (12)); c(i) = A^+ b(i) (Eq. (11)) or the indicator c(i) = e_s
+ *   (Eq. (17)); g_hat = sum_k c_k (omega*(b_k f)) / sum_k c_k (omega*b_k)
+ *   (Eq. (15)-(16)).
+ *
+ * Conventions for every entry point:
+ *   - Images are planar float32, (channels, H, W) row-major, contiguous,
+ *     pixel i = y*W + x.  Guides are planar (rho, H, W), float32 or bfloat16
+ *     (hdf_desc.guide_dtype).  The guide may alias the image (p == f) when
+ *     rho == n and the guide is float32 (plain bilateral filter).
+ *   - Pointers named d_* are DEVICE pointers on the current CUDA device;
+ *     pointers named h_* are HOST pointers.  The caller owns every buffer it
+ *     passes; the library never frees or retains them past the call.
+ *   - `stream` is a cudaStream_t (0 = legacy default stream).  Device work
+ *     is enqueued on it and the call returns without waiting, except where
+ *     the comment says it synchronises.
+ *   - Window outside the image: neighbours outside Omega are left out of
+ *     every sum (zero extension of the convolved images).
+ *   - Errors: every call returns an hdf_status; on anything but HDF_OK no
+ *     device work was enqueued (argument errors) or the CUDA error is
+ *     reported (HDF_ECUDA).  Faults detected on the device (a bounded wait
+ *     that gave up, a capacity overflow) are recorded in the handle's device
+ *     status word and reported by hdf_get_stats.
+ */
+#ifndef HDFILTER_H
+#define HDFILTER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HDF_OK = 0,
+  HDF_EINVAL = 1,        /* bad argument: shape, sigma <= 0, K out of range, NULL */
+  HDF_ENOMEM = 2,        /* device allocation failed in hdf_create */
+  HDF_ECUDA = 3,         /* a CUDA runtime call failed (see hdf_last_cuda_error) */
+  HDF_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
+  HDF_EDOMAIN = 5,       /* non-finite value met where the method needs finite data */
+  HDF_EUNSUPPORTED = 6   /* valid request this build does not handle (e.g. S > 32) */
+} hdf_status;
+
+enum { HDF_GUIDE_F32 = 0, HDF_GUIDE_BF16 = 1 };
+enum { HDF_COEF_OPT = 0,        /* c(i) = A^+ b(i), Eq. (11) */
+       HDF_COEF_INDICATOR = 1   /* c(i) = e_s, s the nearest centre, Eq. (17) */ };
+
+/* Limits of this build. */
+#define HDF_MAX_K 64           /* clusters */
+#define HDF_MAX_RHO 64         /* guide dimensions */
+#define HDF_MAX_S 32           /* window half-width */
+#define HDF_MAX_N 256          /* image channels */
+
+typedef struct {
+  int H, W;          /* image size, H, W >= 1 */
+  int n;             /* channels of f, 1..HDF_MAX_N */
+  int rho;           /* dimensions of the guide p, 1..HDF_MAX_RHO */
+  int K;             /* clusters requested, 1..HDF_MAX_K (K_eff <= K after clustering) */
+  int S;             /* window half-width; 0 selects ceil(3 sigma_s) (Sec. III) */
+  double sigma_s;    /* spatial Gaussian std (pixels), > 0 */
+  double sigma_r;    /* range Gaussian std (guide units), > 0 */
+  int guide_dtype;   /* HDF_GUIDE_F32 or HDF_GUIDE_BF16 */
+  int coef;          /* HDF_COEF_OPT or HDF_COEF_INDICATOR */
+} hdf_desc;
+
+typedef struct hdf_handle hdf_handle;
+
+typedef struct {
+  int K_eff;             /* number of centres in use */
+  int fallback_pixels;   /* pixels of the last hdf_apply that took the denominator guard */
+  int device_error;      /* hdf_status recorded on the device (HDF_OK if none) */
+  int lloyd_iters_max;   /* largest 2-means iteration count of the last clustering */
+  int rounds;            /* parallel split rounds of the last clustering */
+  double cluster_error;  /* E_K = sum_k sum_{i in C_k} |p(i) - mu_k|^2 (Theorem 1) */
+} hdf_stats;
+
+/* Validate `desc`, fill in S if 0, and allocate the device workspace of one
+ * filter instance (centres, A^+, per-pixel range maps and coefficients,
+ * clustering scratch).  Synchronous; the only call that allocates.
+ * Sec. II (Algorithm 1 needs mu, A^+ and the b_k, c_k maps).
+ * Errors: HDF_EINVAL (bad desc), HDF_EUNSUPPORTED (beyond HDF_MAX_*),
+ * HDF_ENOMEM. */
+hdf_status hdf_create(hdf_handle** out, const hdf_desc* desc);
+
+/* Release everything hdf_create allocated.  Synchronises the device. */
+void hdf_destroy(hdf_handle* h);
+
+/* The descriptor in effect (S filled in). */
+hdf_status hdf_get_desc(const hdf_handle* h, hdf_desc* out);
+
+/* Algorithm 1 "cluster" + "pinv": bisecting K-means of Theta = {p(i)}
+ * (Eq. (8), Sec. II-C) on the device, then A (Eq. (12)) and A^+ in FP64.
+ * d_p: guide (rho, H, W) in the handle's guide dtype.  Asynchronous, no host
+ * synchronisation; K_eff stays on the device (read it with hdf_get_stats or
+ * hdf_get_centers). */
+hdf_status hdf_cluster(hdf_handle* h, const void* d_p, void* stream);
+
+/* Install K centres given on the host (K x rho float32, row-major) instead of
+ * clustering, and compute A and A^+ (Eq. (12), Algorithm 1 "pinv").  K <=
+ * desc.K.  Enqueues an async copy from h_mu (the host buffer must stay valid
+ * until the stream reaches it; pageable memory makes it synchronous). */
+hdf_status hdf_set_centers(hdf_handle* h, const float* h_mu, int K, void* stream);
+
+/* Copy the centres (K_eff x rho float32) to h_mu (room for desc.K rows) and
+ * K_eff to *K_eff.  Synchronises `stream`. */
+hdf_status hdf_get_centers(hdf_handle* h, float* h_mu, int* K_eff, void* stream);
+
+/* Copy A^+ (K_eff x K_eff, float64, row-major) to h_out (room for K*K).
+ * Synchronises `stream`. */
+hdf_status hdf_get_pinv(hdf_handle* h, double* h_out, void* stream);
+
+/* Cluster labels of the last hdf_cluster: d_labels[i] in [0, K_eff), the
+ * bisecting partition (Sec. II-C).  d_labels: device int32, H*W. Async. */
+hdf_status hdf_get_labels(hdf_handle* h, int32_t* d_labels, void* stream);
+
+/* Algorithm 1 loops "for1"-"for3": range maps b_k, coefficients c, the
+ * K(n+1) spatial convolutions and the combine/normalise of Eq. (15)-(16),
+ * with the centres installed by hdf_cluster or hdf_set_centers.
+ * d_f: (n, H, W) float32; d_p: guide (rho, H, W); d_g: output (n, H, W)
+ * float32, must not alias d_f or d_p.  Where sum_k c_k r_k <= 1e-6 max_k r_k
+ * the pixel takes the indicator value v_s / r_s (s = nearest centre).
+ * Asynchronous, allocates nothing. */
+hdf_status hdf_apply(hdf_handle* h, const float* d_f, const void* d_p, float* d_g,
+                     void* stream);
+
+/* Gradients of L(g_hat) given G = dL/dg_hat (d_grad_g, (n, H, W)), with the
+ * centres and S held fixed:
+ *   d_grad_f          (n, H, W): dL/df; when d_p == d_f (guide = image) it
+ *                     includes the path through b_k(p) and c(p);
+ *   d_grad_log_sigma  2 float64: dL/dlog sigma_s, dL/dlog sigma_r.
+ * Convolution outputs are recomputed, not stored.  Requires HDF_COEF_OPT and
+ * an A that is full rank under the pinv tolerance (dA^+ of a truncated
+ * pseudo-inverse is not defined): HDF_EDOMAIN is recorded otherwise.
+ * Asynchronous.  Differentiates Eq. (15)-(16); the paper has no backward pass. */
+hdf_status hdf_backward(hdf_handle* h, const float* d_f, const void* d_p,
+                        const float* d_grad_g, float* d_grad_f,
+                        double* d_grad_log_sigma, void* stream);
+
+/* Brute-force filter, Eq. (1)-(2), by direct summation over the window.
+ * Same layouts as hdf_apply.  Asynchronous, allocates nothing. */
+hdf_status hdf_bruteforce(const hdf_desc* desc, const float* d_f, const void* d_p,
+                          float* d_g, void* stream);
+
+/* Statistics and the device status word (see hdf_stats).  Synchronises
+ * `stream`.  Returns the recorded device error, if any. */
+hdf_status hdf_get_stats(hdf_handle* h, hdf_stats* out, void* stream);
+
+/* Human-readable name of a status code. */
+const char* hdf_status_string(hdf_status s);
+
+/* Text of the last CUDA error seen by this thread's calls ("" if none). */
+const char* hdf_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HDFILTER_H */

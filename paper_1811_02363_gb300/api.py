@@ -1,0 +1,172 @@
+"""Python surface of the GB300 fast high-dimensional bilateral / NLM filter.
+
+Thin wrappers over the C ABI (include/hdfilter.h): they check tensor shapes,
+dtypes and devices, pass raw pointers and torch's current CUDA stream, and
+raise on error codes.  PyTorch supplies device memory and streams only; all
+arithmetic runs in libhdfilter's kernels, and there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _stream() -> C.c_void_p:
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t: torch.Tensor) -> C.c_void_p:
+    return C.c_void_p(t.data_ptr())
+
+
+def _check_image(t: torch.Tensor, name: str, dtype=torch.float32) -> None:
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous (planar C x H x W)")
+    if t.dim() != 3:
+        raise ValueError(f"{name} must be (C, H, W)")
+
+
+def window_halfwidth(sigma_s: float) -> int:
+    """S = ceil(3 sigma_s) (Sec. III)."""
+    return int(math.ceil(3.0 * sigma_s))
+
+
+def make_desc(H, W, n, rho, K, sigma_s, sigma_r, S=0, guide_dtype="f32", coef="opt") -> L.hdf_desc:
+    d = L.hdf_desc()
+    d.H, d.W, d.n, d.rho, d.K = int(H), int(W), int(n), int(rho), int(K)
+    d.S = int(S) if S else window_halfwidth(sigma_s)
+    d.sigma_s, d.sigma_r = float(sigma_s), float(sigma_r)
+    d.guide_dtype = {"f32": L.HDF_GUIDE_F32, "bf16": L.HDF_GUIDE_BF16}[guide_dtype]
+    d.coef = {"opt": L.HDF_COEF_OPT, "indicator": L.HDF_COEF_INDICATOR}[coef]
+    return d
+
+
+class HDFilter:
+    """One filter instance (Algorithm 1) for images of a fixed shape.
+
+    ``cluster(p)`` runs bisecting K-means + the FP64 pseudo-inverse on the
+    device; ``set_centers(mu)`` installs given centres instead; ``apply(f, p)``
+    filters; ``backward(...)`` returns gradients."""
+
+    def __init__(self, H, W, n, rho, K, sigma_s, sigma_r, S=0, guide_dtype="f32", coef="opt"):
+        self.desc = make_desc(H, W, n, rho, K, sigma_s, sigma_r, S, guide_dtype, coef)
+        self._h = C.c_void_p()
+        L.check(L.lib().hdf_create(C.byref(self._h), C.byref(self.desc)), "hdf_create")
+        L.check(L.lib().hdf_get_desc(self._h, C.byref(self.desc)), "hdf_get_desc")
+        self.guide_torch_dtype = torch.float32 if guide_dtype == "f32" else torch.bfloat16
+
+    # -- lifecycle
+    def close(self) -> None:
+        if self._h:
+            L.lib().hdf_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def S(self) -> int:
+        return self.desc.S
+
+    def _check_guide(self, p: torch.Tensor) -> None:
+        _check_image(p, "p", self.guide_torch_dtype)
+        if tuple(p.shape) != (self.desc.rho, self.desc.H, self.desc.W):
+            raise ValueError(f"guide shape {tuple(p.shape)} != (rho, H, W)")
+
+    def _check_f(self, f: torch.Tensor, name="f") -> None:
+        _check_image(f, name)
+        if tuple(f.shape) != (self.desc.n, self.desc.H, self.desc.W):
+            raise ValueError(f"{name} shape {tuple(f.shape)} != (n, H, W)")
+
+    # -- Algorithm 1 steps
+    def cluster(self, p: torch.Tensor) -> None:
+        self._check_guide(p)
+        L.check(L.lib().hdf_cluster(self._h, _ptr(p), _stream()), "hdf_cluster")
+
+    def set_centers(self, mu) -> None:
+        mu = np.ascontiguousarray(np.asarray(mu, dtype=np.float32))
+        if mu.ndim != 2 or mu.shape[1] != self.desc.rho:
+            raise ValueError("centres must be (K, rho)")
+        self._mu_keepalive = mu
+        L.check(L.lib().hdf_set_centers(self._h, mu.ctypes.data_as(C.c_void_p), mu.shape[0],
+                                        _stream()), "hdf_set_centers")
+        torch.cuda.current_stream().synchronize()
+
+    def get_centers(self) -> np.ndarray:
+        out = np.zeros((self.desc.K, self.desc.rho), dtype=np.float32)
+        k = C.c_int()
+        L.check(L.lib().hdf_get_centers(self._h, out.ctypes.data_as(C.c_void_p), C.byref(k),
+                                        _stream()), "hdf_get_centers")
+        return out[:k.value].copy()
+
+    def get_pinv(self) -> np.ndarray:
+        out = np.zeros(self.desc.K * self.desc.K, dtype=np.float64)
+        L.check(L.lib().hdf_get_pinv(self._h, out.ctypes.data_as(C.c_void_p), _stream()),
+                "hdf_get_pinv")
+        k = self.stats()["K_eff"]
+        return out[:k * k].reshape(k, k)
+
+    def get_labels(self) -> torch.Tensor:
+        lab = torch.empty(self.desc.H * self.desc.W, dtype=torch.int32, device="cuda")
+        L.check(L.lib().hdf_get_labels(self._h, _ptr(lab), _stream()), "hdf_get_labels")
+        return lab
+
+    def apply(self, f: torch.Tensor, p: torch.Tensor | None = None,
+              out: torch.Tensor | None = None) -> torch.Tensor:
+        self._check_f(f)
+        p = f if p is None else p
+        self._check_guide(p)
+        g = torch.empty_like(f) if out is None else out
+        self._check_f(g, "out")
+        L.check(L.lib().hdf_apply(self._h, _ptr(f), _ptr(p), _ptr(g), _stream()), "hdf_apply")
+        return g
+
+    def backward(self, f: torch.Tensor, p: torch.Tensor, grad_g: torch.Tensor):
+        """Returns (dL/df, dL/dlog sigma_s, dL/dlog sigma_r) as CUDA tensors."""
+        self._check_f(f)
+        self._check_guide(p)
+        self._check_f(grad_g, "grad_g")
+        gf = torch.empty_like(f)
+        gs = torch.zeros(2, dtype=torch.float64, device=f.device)
+        L.check(L.lib().hdf_backward(self._h, _ptr(f), _ptr(p), _ptr(grad_g), _ptr(gf), _ptr(gs),
+                                     _stream()), "hdf_backward")
+        return gf, gs[0], gs[1]
+
+    def stats(self) -> dict:
+        s = L.hdf_stats()
+        code = L.lib().hdf_get_stats(self._h, C.byref(s), _stream())
+        d = {k: getattr(s, k) for k, _ in L.hdf_stats._fields_}
+        if code != L.HDF_OK:
+            raise L.HDFError(code, "device status")
+        return d
+
+
+def bruteforce(f: torch.Tensor, p: torch.Tensor | None, sigma_s: float, sigma_r: float,
+               S: int = 0, out: torch.Tensor | None = None) -> torch.Tensor:
+    """Eq. (1)-(2) by direct summation on the GPU."""
+    _check_image(f, "f")
+    p = f if p is None else p
+    if not p.is_cuda or p.dim() != 3 or not p.is_contiguous():
+        raise ValueError("p must be a contiguous CUDA (rho, H, W) tensor")
+    if p.dtype not in (torch.float32, torch.bfloat16):
+        raise ValueError("p must be float32 or bfloat16")
+    n, H, W = f.shape
+    d = make_desc(H, W, n, p.shape[0], 1, sigma_s, sigma_r, S,
+                  "f32" if p.dtype == torch.float32 else "bf16")
+    g = torch.empty_like(f) if out is None else out
+    _check_image(g, "out")
+    L.check(L.lib().hdf_bruteforce(C.byref(d), _ptr(f), _ptr(p), _ptr(g), _stream()),
+            "hdf_bruteforce")
+    return g

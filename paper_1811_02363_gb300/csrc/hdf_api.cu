@@ -1,0 +1,243 @@
+// C ABI entry points of libhdfilter (declared in include/hdfilter.h):
+// argument checking, workspace ownership and the order of the device stages
+// of Algorithm 1.  The arithmetic lives in the k_*.cu kernels.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "hdf_internal.cuh"
+
+namespace {
+
+thread_local char g_cuda_err[256] = "";
+
+hdf_status cuda_fail(cudaError_t e, const char* where) {
+  snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", where, cudaGetErrorString(e));
+  return HDF_ECUDA;
+}
+
+#define HDF_CUDA(call, where)                       \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+hdf_status check_desc(hdf_desc* d) {
+  if (!d) return HDF_EINVAL;
+  if (d->H < 1 || d->W < 1 || d->n < 1 || d->rho < 1 || d->K < 1) return HDF_EINVAL;
+  if (!(d->sigma_s > 0.0) || !(d->sigma_r > 0.0) || !isfinite(d->sigma_s) ||
+      !isfinite(d->sigma_r))
+    return HDF_EINVAL;
+  if (d->S < 0) return HDF_EINVAL;
+  if (d->S == 0) d->S = (int)ceil(3.0 * d->sigma_s);
+  if (d->guide_dtype != HDF_GUIDE_F32 && d->guide_dtype != HDF_GUIDE_BF16) return HDF_EINVAL;
+  if (d->coef != HDF_COEF_OPT && d->coef != HDF_COEF_INDICATOR) return HDF_EINVAL;
+  if (d->K > HDF_MAX_K || d->rho > HDF_MAX_RHO || d->S > HDF_MAX_S || d->n > HDF_MAX_N)
+    return HDF_EUNSUPPORTED;
+  if ((long long)d->H * d->W >= (1LL << 31)) return HDF_EUNSUPPORTED;
+  return HDF_OK;
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, count * sizeof(T) + 16);
+}
+
+}  // namespace
+
+namespace hdf {
+
+Taps make_taps(double sigma_s, int S) {
+  Taps t;
+  memset(&t, 0, sizeof(t));
+  for (int j = -S; j <= S; ++j) t.w[j + S] = (float)exp(-(double)(j * j) / (2.0 * sigma_s * sigma_s));
+  return t;
+}
+
+}  // namespace hdf
+
+extern "C" {
+
+const char* hdf_status_string(hdf_status s) {
+  switch (s) {
+    case HDF_OK: return "HDF_OK";
+    case HDF_EINVAL: return "HDF_EINVAL: invalid argument";
+    case HDF_ENOMEM: return "HDF_ENOMEM: device allocation failed";
+    case HDF_ECUDA: return "HDF_ECUDA: CUDA runtime error";
+    case HDF_ETIMEOUT: return "HDF_ETIMEOUT: bounded device wait gave up";
+    case HDF_EDOMAIN: return "HDF_EDOMAIN: input outside the method's domain";
+    case HDF_EUNSUPPORTED: return "HDF_EUNSUPPORTED: beyond this build's limits";
+  }
+  return "unknown hdf_status";
+}
+
+const char* hdf_last_cuda_error(void) { return g_cuda_err; }
+
+hdf_status hdf_create(hdf_handle** out, const hdf_desc* desc) {
+  if (!out || !desc) return HDF_EINVAL;
+  *out = nullptr;
+  hdf_desc d = *desc;
+  hdf_status st = check_desc(&d);
+  if (st != HDF_OK) return st;
+  hdf_handle* h = new (std::nothrow) hdf_handle;
+  if (!h) return HDF_ENOMEM;
+  memset(h, 0, sizeof(*h));
+  h->d = d;
+  h->N = d.H * d.W;
+  HDF_CUDA(cudaGetDevice(&h->device), "cudaGetDevice");
+  const size_t N = (size_t)h->N, K = (size_t)d.K, R = (size_t)d.rho;
+  bool ok = true;
+  ok &= dalloc(&h->ctrl, hdf::CTRL_WORDS) == cudaSuccess;
+  ok &= dalloc(&h->mu, K * R) == cudaSuccess;
+  ok &= dalloc(&h->mu64, K * R) == cudaSuccess;
+  ok &= dalloc(&h->pinv64, K * K) == cudaSuccess;
+  ok &= dalloc(&h->pinv32, K * K) == cudaSuccess;
+  ok &= dalloc(&h->ek, 1) == cudaSuccess;
+  ok &= dalloc(&h->B, K * N) == cudaSuccess;
+  ok &= dalloc(&h->C, K * N) == cudaSuccess;
+  ok &= dalloc(&h->s, N) == cudaSuccess;
+  ok &= dalloc(&h->fix_list, N) == cudaSuccess;
+  ok &= dalloc(&h->grad_scratch, 1 << 16) == cudaSuccess;
+  ok &= dalloc(&h->labels, N) == cudaSuccess;
+  h->cl_ws_bytes = hdf::cluster_workspace_bytes(h->N, d.rho, d.K);
+  ok &= cudaMalloc(&h->cl_ws, h->cl_ws_bytes) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    hdf_destroy(h);
+    return HDF_ENOMEM;
+  }
+  if (cudaMemset(h->ctrl, 0, hdf::CTRL_WORDS * sizeof(int)) != cudaSuccess ||
+      cudaMemset(h->mu, 0, K * R * sizeof(float)) != cudaSuccess ||
+      cudaMemset(h->ek, 0, sizeof(double)) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {
+    hdf_destroy(h);
+    return cuda_fail(cudaGetLastError(), "hdf_create init");
+  }
+  *out = h;
+  return HDF_OK;
+}
+
+void hdf_destroy(hdf_handle* h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  cudaFree(h->ctrl);
+  cudaFree(h->mu);
+  cudaFree(h->mu64);
+  cudaFree(h->pinv64);
+  cudaFree(h->pinv32);
+  cudaFree(h->ek);
+  cudaFree(h->B);
+  cudaFree(h->C);
+  cudaFree(h->s);
+  cudaFree(h->fix_list);
+  cudaFree(h->grad_scratch);
+  cudaFree(h->labels);
+  cudaFree(h->cl_ws);
+  delete h;
+}
+
+hdf_status hdf_get_desc(const hdf_handle* h, hdf_desc* out) {
+  if (!h || !out) return HDF_EINVAL;
+  *out = h->d;
+  return HDF_OK;
+}
+
+hdf_status hdf_cluster(hdf_handle* h, const void* d_p, void* stream) {
+  if (!h || !d_p) return HDF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  HDF_CUDA(hdf::launch_cluster(h, d_p, st), "cluster");
+  HDF_CUDA(hdf::launch_fit(h, st), "fit");
+  return HDF_OK;
+}
+
+hdf_status hdf_set_centers(hdf_handle* h, const float* h_mu, int K, void* stream) {
+  if (!h || !h_mu || K < 1 || K > h->d.K) return HDF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = (size_t)K * h->d.rho * sizeof(float);
+  HDF_CUDA(cudaMemcpyAsync(h->mu, h_mu, bytes, cudaMemcpyHostToDevice, st), "set_centers copy");
+  HDF_CUDA(hdf::launch_set_int(h->ctrl + hdf::CTRL_K_EFF, K, st), "set_centers K");
+  HDF_CUDA(hdf::launch_fit(h, st), "fit");
+  return HDF_OK;
+}
+
+hdf_status hdf_get_centers(hdf_handle* h, float* h_mu, int* K_eff, void* stream) {
+  if (!h || !h_mu || !K_eff) return HDF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  int k = 0;
+  HDF_CUDA(cudaMemcpyAsync(&k, h->ctrl + hdf::CTRL_K_EFF, sizeof(int), cudaMemcpyDeviceToHost, st),
+           "get K");
+  HDF_CUDA(cudaMemcpyAsync(h_mu, h->mu, (size_t)h->d.K * h->d.rho * sizeof(float),
+                           cudaMemcpyDeviceToHost, st),
+           "get centers");
+  HDF_CUDA(cudaStreamSynchronize(st), "sync");
+  *K_eff = k;
+  return HDF_OK;
+}
+
+hdf_status hdf_get_pinv(hdf_handle* h, double* h_out, void* stream) {
+  if (!h || !h_out) return HDF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  HDF_CUDA(cudaMemcpyAsync(h_out, h->pinv64, (size_t)h->d.K * h->d.K * sizeof(double),
+                           cudaMemcpyDeviceToHost, st),
+           "get pinv");
+  HDF_CUDA(cudaStreamSynchronize(st), "sync");
+  return HDF_OK;
+}
+
+hdf_status hdf_get_labels(hdf_handle* h, int32_t* d_labels, void* stream) {
+  if (!h || !d_labels) return HDF_EINVAL;
+  HDF_CUDA(cudaMemcpyAsync(d_labels, h->labels, (size_t)h->N * sizeof(int32_t),
+                           cudaMemcpyDeviceToDevice, (cudaStream_t)stream),
+           "get labels");
+  return HDF_OK;
+}
+
+hdf_status hdf_apply(hdf_handle* h, const float* d_f, const void* d_p, float* d_g, void* stream) {
+  if (!h || !d_f || !d_p || !d_g) return HDF_EINVAL;
+  if ((const void*)d_g == (const void*)d_f || (const void*)d_g == d_p) return HDF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  HDF_CUDA(hdf::launch_rangemap(h, d_p, st), "rangemap");
+  HDF_CUDA(hdf::launch_filter(h, d_f, d_g, st), "filter");
+  return HDF_OK;
+}
+
+hdf_status hdf_backward(hdf_handle* h, const float* d_f, const void* d_p, const float* d_grad_g,
+                        float* d_grad_f, double* d_grad_log_sigma, void* stream) {
+  if (!h || !d_f || !d_p || !d_grad_g || !d_grad_f || !d_grad_log_sigma) return HDF_EINVAL;
+  if (h->d.coef != HDF_COEF_OPT) return HDF_EUNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  HDF_CUDA(hdf::launch_backward(h, d_f, d_p, d_grad_g, d_grad_f, d_grad_log_sigma, st),
+           "backward");
+  return HDF_OK;
+}
+
+hdf_status hdf_bruteforce(const hdf_desc* desc, const float* d_f, const void* d_p, float* d_g,
+                          void* stream) {
+  if (!desc || !d_f || !d_p || !d_g) return HDF_EINVAL;
+  hdf_desc d = *desc;
+  hdf_status s = check_desc(&d);
+  if (s != HDF_OK) return s;
+  HDF_CUDA(hdf::launch_bruteforce(d, d_f, d_p, d_g, (cudaStream_t)stream), "bruteforce");
+  return HDF_OK;
+}
+
+hdf_status hdf_get_stats(hdf_handle* h, hdf_stats* out, void* stream) {
+  if (!h || !out) return HDF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  int c[hdf::CTRL_WORDS];
+  double ek = 0.0;
+  HDF_CUDA(cudaMemcpyAsync(c, h->ctrl, sizeof(c), cudaMemcpyDeviceToHost, st), "stats");
+  HDF_CUDA(cudaMemcpyAsync(&ek, h->ek, sizeof(double), cudaMemcpyDeviceToHost, st), "stats");
+  HDF_CUDA(cudaStreamSynchronize(st), "sync");
+  out->K_eff = c[hdf::CTRL_K_EFF];
+  out->device_error = c[hdf::CTRL_ERROR];
+  out->fallback_pixels = c[hdf::CTRL_FALLBACK];
+  out->lloyd_iters_max = c[hdf::CTRL_LLOYD_MAX];
+  out->rounds = c[hdf::CTRL_ROUNDS];
+  out->cluster_error = ek;
+  return (hdf_status)c[hdf::CTRL_ERROR];
+}
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// Internal declarations shared by the translation units of libhdfilter.
+// Nothing here is part of the C ABI (include/hdfilter.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/hdfilter.h"
+
+namespace hdf {
+
+// Device control words of one handle (int32 unless noted).
+enum CtrlSlot {
+  CTRL_K_EFF = 0,        // centres in use
+  CTRL_ERROR = 1,        // first hdf_status recorded on the device
+  CTRL_FALLBACK = 2,     // pixels that took the denominator guard in the last apply
+  CTRL_LLOYD_MAX = 3,    // largest 2-means iteration count of the last clustering
+  CTRL_ROUNDS = 4,       // split rounds of the last clustering
+  CTRL_BARRIER = 8,      // grid barrier: arrival counter
+  CTRL_BARRIER_GEN = 9,  // grid barrier: generation
+  CTRL_WORDS = 16
+};
+
+// Record `code` as the device error unless one is already recorded.
+__device__ __forceinline__ void record_error(int* ctrl, int code) {
+  atomicCAS(ctrl + CTRL_ERROR, 0, code);
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Guide element as float for either storage type.
+__device__ __forceinline__ float guide_load(const float* p, size_t i) { return __ldg(p + i); }
+__device__ __forceinline__ float guide_load(const __nv_bfloat16* p, size_t i) {
+  return __bfloat162float(p[i]);
+}
+
+// Spatial weights of one filter call: omega_1(t) for t = -S..S stored at
+// [t + S]; passed by value so that the taps sit in the constant bank.
+struct Taps {
+  float w[2 * HDF_MAX_S + 1];
+};
+
+}  // namespace hdf
+
+// The handle.  Device buffers sized for desc.K, desc.rho, H*W at create time.
+struct hdf_handle {
+  hdf_desc d;
+  int N;              // H * W
+  int device;         // CUDA device the buffers live on
+  int* ctrl;          // CTRL_WORDS control words
+  float* mu;          // K x rho centres (float32, what the filter uses)
+  double* mu64;       // K x rho centres before rounding (clustering means)
+  double* pinv64;     // K x K A^+ (float64)
+  float* pinv32;      // K x K A^+ rounded to float32
+  double* ek;         // E_K of the last clustering
+  float* B;           // K x N range maps b_k(i)
+  float* C;           // K x N coefficients c_k(i)
+  uint8_t* s;         // N nearest centre (Voronoi cell) per pixel
+  int* fix_list;      // N pixels that take the denominator guard
+  double* grad_scratch;  // backward partial sums
+  // clustering workspace (allocated in hdf_create, sized by N)
+  void* cl_ws;
+  size_t cl_ws_bytes;
+  int32_t* labels;    // N labels of the last clustering
+};
+
+namespace hdf {
+
+// Launchers (each returns cudaGetLastError() of its launch).
+cudaError_t launch_fit(hdf_handle* h, cudaStream_t st);           // A, A^+ from h->mu
+cudaError_t launch_set_int(int* p, int v, cudaStream_t st);
+cudaError_t launch_rangemap(hdf_handle* h, const void* p, cudaStream_t st);
+cudaError_t launch_filter(hdf_handle* h, const float* f, float* g, cudaStream_t st);
+cudaError_t launch_bruteforce(const hdf_desc& d, const float* f, const void* p, float* g,
+                              cudaStream_t st);
+cudaError_t launch_cluster(hdf_handle* h, const void* p, cudaStream_t st);
+size_t cluster_workspace_bytes(int N, int rho, int K);
+cudaError_t launch_backward(hdf_handle* h, const float* f, const void* p, const float* G,
+                            float* grad_f, double* grad_ls, cudaStream_t st);
+
+// Host helpers.
+Taps make_taps(double sigma_s, int S);
+
+}  // namespace hdf

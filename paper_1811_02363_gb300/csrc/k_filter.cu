@@ -1,0 +1,168 @@
+// Algorithm 1 loops "for1" and "for2" (range maps b_k and coefficients c),
+// the guard fix-up, and the dispatch of the fused convolution/combine tile
+// kernel (filter_tile.cuh) for hdf_apply.
+#include <math.h>
+
+#include "filter_tile.cuh"
+#include "hdf_internal.cuh"
+
+namespace hdf {
+namespace {
+
+constexpr int RM_THREADS = 256;
+
+// b_k(i) = phi(mu_k - p(i)) (Eq. (12)), computed from direct differences in
+// FP32; c(i) = A^+ b(i) (Eq. (11)) or e_s (Eq. (17)); s(i) = nearest centre
+// (ties -> lowest k).
+template <int KMAX, typename GT>
+__global__ void __launch_bounds__(RM_THREADS)
+rangemap_kernel(const GT* __restrict__ p, int N, int rho, const float* __restrict__ mu,
+                const float* __restrict__ pinv, const int* __restrict__ ctrl, float inv2sr2,
+                int coef, float* __restrict__ B, float* __restrict__ C,
+                uint8_t* __restrict__ s_out) {
+  extern __shared__ float sm[];
+  const int K = ctrl[CTRL_K_EFF];
+  float* smu = sm;                 // K x rho
+  float* spi = sm + K * rho;       // K x K
+  for (int i = threadIdx.x; i < K * rho; i += blockDim.x) smu[i] = mu[i];
+  for (int i = threadIdx.x; i < K * K; i += blockDim.x) spi[i] = pinv[i];
+  __syncthreads();
+  const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= N) return;
+  float d2[KMAX];
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) d2[k] = 0.0f;
+  for (int d = 0; d < rho; ++d) {
+    const float x = guide_load(p, (size_t)d * N + pix);
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+      if (k < K) {
+        const float t = x - smu[k * rho + d];
+        d2[k] = fmaf(t, t, d2[k]);
+      }
+    }
+  }
+  int s = 0;
+  float best = d2[0];
+#pragma unroll
+  for (int k = 1; k < KMAX; ++k)
+    if (k < K && d2[k] < best) { best = d2[k]; s = k; }
+  float b[KMAX];
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) b[k] = (k < K) ? expf(-d2[k] * inv2sr2) : 0.0f;
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k)
+    if (k < K) B[(size_t)k * N + pix] = b[k];
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) {
+    if (k < K) {
+      float c;
+      if (coef == HDF_COEF_OPT) {
+        c = 0.0f;
+#pragma unroll
+        for (int l = 0; l < KMAX; ++l)
+          if (l < K) c = fmaf(spi[k * K + l], b[l], c);
+      } else {
+        c = (k == s) ? 1.0f : 0.0f;
+      }
+      C[(size_t)k * N + pix] = c;
+    }
+  }
+  s_out[pix] = (uint8_t)s;
+}
+
+template <int KMAX>
+cudaError_t launch_rm(hdf_handle* h, const void* p, cudaStream_t st) {
+  const hdf_desc& d = h->d;
+  const size_t smem = sizeof(float) * ((size_t)d.K * d.rho + (size_t)d.K * d.K);
+  const float inv2sr2 = (float)(1.0 / (2.0 * d.sigma_r * d.sigma_r));
+  const int grid = (h->N + RM_THREADS - 1) / RM_THREADS;
+  if (d.guide_dtype == HDF_GUIDE_BF16)
+    rangemap_kernel<KMAX, __nv_bfloat16><<<grid, RM_THREADS, smem, st>>>(
+        (const __nv_bfloat16*)p, h->N, d.rho, h->mu, h->pinv32, h->ctrl, inv2sr2, d.coef, h->B,
+        h->C, h->s);
+  else
+    rangemap_kernel<KMAX, float><<<grid, RM_THREADS, smem, st>>>(
+        (const float*)p, h->N, d.rho, h->mu, h->pinv32, h->ctrl, inv2sr2, d.coef, h->B, h->C,
+        h->s);
+  return cudaGetLastError();
+}
+
+// Pixels where the denominator guard fired take the indicator value
+// v_s(i) / r_s(i) of Eq. (18) (s = nearest centre), computed here by direct
+// sums over the window from the stored b_s plane; f(i) if r_s(i) = 0.
+__global__ void fixup_kernel(const float* __restrict__ f, const float* __restrict__ B,
+                             const uint8_t* __restrict__ s, const int* __restrict__ fix_list,
+                             const int* __restrict__ ctrl, int H, int W, int n, int S,
+                             const Taps taps, float* __restrict__ g) {
+  const size_t N = (size_t)H * W;
+  int count = ctrl[CTRL_FALLBACK];
+  if (count > (int)N) count = (int)N;
+  const long long total = (long long)count * n;
+  for (long long item = blockIdx.x * (long long)blockDim.x + threadIdx.x; item < total;
+       item += (long long)gridDim.x * blockDim.x) {
+    const int idx = (int)(item / n), ch = (int)(item % n);
+    const int pix = fix_list[idx];
+    const int y = pix / W, x = pix % W;
+    const float* Bs = B + (size_t)s[pix] * N;
+    const float* fc = f + (size_t)ch * N;
+    float r = 0.0f, v = 0.0f;
+    for (int j1 = -S; j1 <= S; ++j1) {
+      const int yy = y - j1;
+      if (yy < 0 || yy >= H) continue;
+      for (int j2 = -S; j2 <= S; ++j2) {
+        const int xx = x - j2;
+        if (xx < 0 || xx >= W) continue;
+        const float w = taps.w[j1 + S] * taps.w[j2 + S] * Bs[(size_t)yy * W + xx];
+        r += w;
+        v = fmaf(w, fc[(size_t)yy * W + xx], v);
+      }
+    }
+    g[(size_t)ch * N + pix] = (r > 0.0f) ? v / r : fc[pix];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_rangemap(hdf_handle* h, const void* p, cudaStream_t st) {
+  const int K = h->d.K;
+  if (K <= 8) return launch_rm<8>(h, p, st);
+  if (K <= 16) return launch_rm<16>(h, p, st);
+  if (K <= 32) return launch_rm<32>(h, p, st);
+  return launch_rm<64>(h, p, st);
+}
+
+// Compiled half-widths of the tile kernel; a call's S runs on the smallest
+// bucket >= S with zero weights beyond S.
+static const int kBuckets[] = {3, 6, 9, 12, 15, 18, 24, 32};
+
+int filter_bucket(int S) {
+  for (int b : kBuckets)
+    if (S <= b) return b;
+  return -1;
+}
+
+cudaError_t launch_filter(hdf_handle* h, const float* f, float* g, cudaStream_t st) {
+  const hdf_desc& d = h->d;
+  const int SB = filter_bucket(d.S);
+  if (SB < 0) return cudaErrorInvalidValue;
+  const int P = (d.n == 1 || SB > 16) ? 2 : 4;
+  // Taps centred in the bucket: w[SB + j] = omega_1(j) for |j| <= S, 0 beyond.
+  Taps exact = make_taps(d.sigma_s, d.S);
+  Taps taps;
+  for (int t = 0; t < 2 * HDF_MAX_S + 1; ++t) taps.w[t] = 0.0f;
+  for (int j = -d.S; j <= d.S; ++j) taps.w[SB + j] = exact.w[d.S + j];
+  cudaError_t e = cudaMemsetAsync(h->ctrl + CTRL_FALLBACK, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  FilterArgs a{f, h->B, h->C, g, h->ctrl, h->fix_list, d.H, d.W, d.n};
+  e = launch_filter_sb(SB, P, a, taps, st);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  fixup_kernel<<<sms, 256, 0, st>>>(f, h->B, h->s, h->fix_list, h->ctrl, d.H, d.W, d.n, d.S,
+                                    exact, g);
+  return cudaGetLastError();
+}
+
+}  // namespace hdf

@@ -1,0 +1,55 @@
+"""The C-ABI library builds, loads and exports every function that
+include/hdfilter.h declares; argument errors are reported before any device
+work.  CPU only: no call here reaches the GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1811_02363_gb300 import build
+    build.build()
+    from paper_1811_02363_gb300 import _lib
+    return _lib
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "hdfilter.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hdf_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported_and_bound(L):
+    names = _declared()
+    assert "hdf_apply" in names and "hdf_create" in names
+    bound = {s[0] for s in L.SIGNATURES}
+    for name in names:
+        assert hasattr(L.lib(), name), name
+        assert name in bound, name
+
+
+def test_argument_errors_without_device_work(L):
+    lib = L.lib()
+    d = L.hdf_desc(H=8, W=8, n=3, rho=3, K=4, S=0, sigma_s=1.0, sigma_r=0.1,
+                   guide_dtype=0, coef=0)
+    h = C.c_void_p()
+    bad = L.hdf_desc.from_buffer_copy(d)
+    bad.H = 0
+    assert lib.hdf_create(C.byref(h), C.byref(bad)) == L.HDF_EINVAL
+    bad = L.hdf_desc.from_buffer_copy(d)
+    bad.sigma_r = -1.0
+    assert lib.hdf_create(C.byref(h), C.byref(bad)) == L.HDF_EINVAL
+    bad = L.hdf_desc.from_buffer_copy(d)
+    bad.K = L.HDF_MAX_K + 1
+    assert lib.hdf_create(C.byref(h), C.byref(bad)) == L.HDF_EUNSUPPORTED
+    bad = L.hdf_desc.from_buffer_copy(d)
+    bad.S = L.HDF_MAX_S + 1
+    assert lib.hdf_create(C.byref(h), C.byref(bad)) == L.HDF_EUNSUPPORTED
+    assert lib.hdf_bruteforce(C.byref(d), None, None, None, None) == L.HDF_EINVAL
+    assert lib.hdf_apply(None, None, None, None, None) == L.HDF_EINVAL
+    assert lib.hdf_status_string(L.HDF_ETIMEOUT).startswith(b"HDF_ETIMEOUT")

@@ -155,6 +155,15 @@ hdf_status hdf_backward(hdf_handle* h, const float* d_f, const void* d_p,
 hdf_status hdf_bruteforce(const hdf_desc* desc, const float* d_f, const void* d_p,
                           float* d_g, void* stream);
 
+/* Phase trace of the last hdf_cluster: up to `cap` events, each two int64
+ * (phase id, device globaltimer in ns) recorded by block 0 at every grid
+ * barrier of the clustering kernel.  Phase ids: 1 root sums, 2 distance
+ * pass, 3 farthest-point pass, 4 root node, 5 Lloyd iteration, 6 partition
+ * count, 7 partition scatter, 8 children written.  h_events: host, room for
+ * 2*cap int64.  *count = events written.  Synchronises `stream`.  Tracing
+ * support; not part of the paper's method. */
+hdf_status hdf_get_trace(hdf_handle* h, int64_t* h_events, int cap, int* count, void* stream);
+
 /* Statistics and the device status word (see hdf_stats).  Synchronises
  * `stream`.  Returns the recorded device error, if any. */
 hdf_status hdf_get_stats(hdf_handle* h, hdf_stats* out, void* stream);

@@ -144,6 +144,14 @@ class HDFilter:
                                      _stream()), "hdf_backward")
         return gf, gs[0], gs[1]
 
+    def trace(self, cap: int = 2048) -> np.ndarray:
+        """(phase, ns) events of the last clustering (see hdf_get_trace)."""
+        buf = np.zeros(2 * cap, dtype=np.int64)
+        n = C.c_int()
+        L.check(L.lib().hdf_get_trace(self._h, buf.ctypes.data_as(C.c_void_p), cap, C.byref(n),
+                                      _stream()), "hdf_get_trace")
+        return buf[:2 * n.value].reshape(-1, 2)
+
     def stats(self) -> dict:
         s = L.hdf_stats()
         code = L.lib().hdf_get_stats(self._h, C.byref(s), _stream())

@@ -1,0 +1,1367 @@
+// Device code of Algorithm 1 "cluster": bisecting K-means of the range set
+// Theta = {p(i)} (Eq. (8), Sec. II-C), entirely on the device in one
+// cooperative persistent launch (no host round trip, graph-capturable).
+//
+// Method (paper): start from one cluster; repeatedly split the cluster of
+// largest variance into two by 2-means, initialised with a pair of points
+// of largest separation, until there are K clusters.  Readings shared with
+// the FP64 oracle: variance = sum of squared deviations (SSE), ties -> lowest
+// cluster index, stop early when the largest SSE is 0; initial pair a = the
+// point farthest from the mean, b = the point farthest from a (ties -> first
+// in raster order); Lloyd iterations assign each point to the nearer centre
+// (ties -> a), stop when no assignment changes or after 20 assignments, and
+// keep the previous assignment if a side would become empty; child 1 keeps
+// the parent's index, child 2 takes the next one.
+//
+// GPU design.  The split of a cluster depends only on that cluster's points,
+// so the split tree is a deterministic function of the data.  Each round
+// replays the sequential greedy rule (largest SSE first) on the part of the
+// tree computed so far and collects every node the replay would split next
+// without knowing its children; all of them are split together in that round
+// (segments of one permutation array, one pass over all their points per
+// Lloyd iteration).  The final replay on the complete tree yields exactly the
+// sequential algorithm's clusters and numbering.  Splits a later replay does
+// not use are simply ignored.
+//
+// Precision: distances in FP32 from direct differences; every integer
+// decision is taken in FP64 where FP32 cannot settle it (Lloyd assignments
+// within 2^-14 relative of a tie, farthest-point candidates within 2^-12 of
+// the maximum).  Coordinate sums are accumulated error-free per thread
+// (TwoSum pairs), then in FP64 across threads and blocks in a fixed order, so
+// the means match a plain FP64 evaluation to rounding and are exact for
+// clusters of identical points (deterministic for a given grid).  The points
+// are kept in a planar copy permuted with the clusters, so every pass reads
+// them coalesced.
+//
+// Synchronisation: a grid barrier with a bounded wait (2 s), after which the
+// device status records HDF_ETIMEOUT and every block returns.  Reductions
+// across blocks are replayed identically by every block from the per-block
+// partial results, so block-local copies of the control state agree.
+#pragma once
+
+#include <math.h>
+
+#include "hdf_internal.cuh"
+
+namespace hdf {
+namespace clus {
+
+
+constexpr int CL_THREADS = 256;
+constexpr int CL_WARPS = CL_THREADS / 32;
+constexpr int PPT = 8;                  // points per thread per chunk
+constexpr int CH = CL_THREADS * PPT;    // points per chunk
+constexpr int MAXACT = 32;              // splits per round
+constexpr int MAXSEG = 2 * MAXACT;
+constexpr int MAXNODES = 16 * HDF_MAX_K;
+constexpr int MAX_LLOYD = 20;
+constexpr unsigned long long BARRIER_NS = 2000000000ull;
+constexpr float TIE_REL = 1.0f / 16384.0f;      // 2^-14: Lloyd recheck band
+constexpr float CAND_REL = 1.0f / 4096.0f;      // 2^-12: farthest-point candidates
+constexpr int TRACE_CAP = 2048;                  // trace events per launch
+constexpr float MARGIN_REL = 1.0f / 4096.0f;    // 2^-12: rounding allowance of a stored margin
+constexpr double ROUND_UP = 1.0 + 1.0 / 1048576.0;
+
+// Phases recorded in the trace (one event per grid barrier passed by block 0).
+enum TracePhase { TR_ROOT = 1, TR_DIST1 = 2, TR_DIST2 = 3, TR_NODE = 4, TR_LLOYD = 5,
+                  TR_COUNT = 6, TR_SCATTER = 7, TR_CHILD = 8, TR_LPASS = 9, TR_LREPLAY = 10,
+                  TR_LUPDATE = 11, TR_LPUB = 12 };
+
+// Record a trace event from block 0 outside a barrier.
+__device__ __forceinline__ void trace_event(long long* trace, int phase) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const long long n = trace[0];
+    if (n < TRACE_CAP) {
+      trace[1 + 2 * n] = phase;
+      trace[2 + 2 * n] = (long long)globaltimer_ns();
+      trace[0] = n + 1;
+    }
+  }
+}
+
+struct NodeRec {
+  int start, count;   // segment of the permutation
+  int child0;         // first child (-1: not split); child 2 = child0 + 1
+  int far_idx;        // raster index of the point farthest from the mean
+  double sse;         // sum of squared deviations (0: never split)
+};
+
+struct SlotRec {      // a split in flight (block-local copy, identical in every block)
+  int node, start, count;
+  int a_idx, b_idx;
+  int done, iters, rev_it;   // rev_it: iteration whose changes were undone (-1: none)
+  int cnt_b_cur, cnt_b_acc;
+  int split;          // produces children
+  int recompute;      // centres to be recomputed from the assignment just made
+};
+
+struct ClArgs {
+  const void* p;
+  int p_bf16;         // guide stored as bfloat16
+  int N, rho, K, G;
+  int* ctrl;
+  float* mu;          // out: K x rho
+  double* mu64;       // out: K x rho
+  int32_t* labels;    // out: N
+  double* ek;         // out: E_K
+  uint32_t* perm;     // N
+  uint32_t* perm2;    // N
+  float* X;           // rho x N points in permutation order
+  float* X2;          // rho x N scatter target
+  uint8_t* side;      // 2 x N
+  float* marg;        // N margin bound + total centre movement when it was computed
+  float* d32;         // N
+  NodeRec* nodes;     // MAXNODES
+  double* node_sum;   // MAXNODES x rho coordinate sums
+  float* pf;          // G x MAXSEG x (rho + 1) double-float pairs
+  int* pi;            // G x MAXSEG x 2
+  float* pd;          // G x MAXSEG
+  double* pdd;        // G x MAXSEG
+  int* px;            // G x MAXSEG
+  int* chunk_cnt;     // max chunks
+  long long* trace;   // [0] = count, then (phase, ns) pairs, block 0 only
+  double* fin;        // MAXACT x (rho + 2) reduced Lloyd sums, published by the owner blocks
+};
+
+}  // namespace clus
+
+namespace clus {
+namespace {
+
+struct ClShared {
+  int seg_start[MAXSEG], seg_count[MAXSEG], seg_chunk0[MAXSEG + 1], seg_on[MAXSEG];
+  int nseg, nchunks;
+  SlotRec slot[MAXACT];
+  int nslots;
+  double sim_sse[MAXNODES];
+  int sim_child0[MAXNODES];
+  int leaf_node[HDF_MAX_K], leaf_cl[HDF_MAX_K];
+  int nleaves, nclusters, nneeded;
+  int needed[MAXACT];
+  float redg[CL_WARPS][2 * HDF_MAX_RHO];
+  float redf[CL_WARPS][1];
+  int redi[CL_WARPS][2];
+  float redd[CL_WARPS];
+  double redD[CL_WARPS];
+  int redx[CL_WARPS];
+  int scanw[CL_WARPS];
+  int hlist[CH];          // positions of a chunk that need the full test
+  float segmax[MAXSEG];
+  float slack[MAXACT];   // centre movement of the last update
+  double cum[MAXACT];    // total centre movement since the split started
+  float cabs[MAXACT];    // absolute allowance for the float32 rounding of the centres
+  double segsse[MAXSEG];
+  int segarg[MAXSEG];
+  int ok;
+  int all_done;
+};
+
+__device__ __forceinline__ bool better(double d1, int i1, double d2, int i2) {
+  return d1 > d2 || (d1 == d2 && i1 < i2);
+}
+
+// Grid barrier with a bounded wait.  Returns false if the device status
+// records an error (this block or another gave up), in which case the
+// caller returns.
+__device__ bool grid_barrier(const ClArgs& a, unsigned& gen, ClShared& s, int phase) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned* cnt = (unsigned*)(a.ctrl + CTRL_BARRIER);
+    volatile unsigned* vgen = (volatile unsigned*)(a.ctrl + CTRL_BARRIER_GEN);
+    __threadfence();
+    const unsigned arrived = atomicAdd(cnt, 1u);
+    if (arrived == (unsigned)a.G - 1) {
+      atomicExch(cnt, 0u);
+      __threadfence();
+      atomicAdd((unsigned*)(a.ctrl + CTRL_BARRIER_GEN), 1u);
+    } else {
+      const unsigned long long t0 = globaltimer_ns();
+      while (*vgen == gen) {
+        __nanosleep(32);
+        if (globaltimer_ns() - t0 > BARRIER_NS) {
+          record_error(a.ctrl, HDF_ETIMEOUT);
+          break;
+        }
+      }
+    }
+    __threadfence();
+    ++gen;
+    s.ok = (*(volatile int*)(a.ctrl + CTRL_ERROR) == 0);
+    if (blockIdx.x == 0) {
+      const long long n = a.trace[0];
+      if (n < TRACE_CAP) {
+        a.trace[1 + 2 * n] = phase;
+        a.trace[2 + 2 * n] = (long long)globaltimer_ns();
+        a.trace[0] = n + 1;
+      }
+    }
+  }
+  __syncthreads();
+  return s.ok != 0;
+}
+
+// Guide element (raster layout) as float, for either storage type.
+__device__ __forceinline__ float guide_at(const ClArgs& a, size_t i) {
+  return a.p_bf16 ? __bfloat162float(((const __nv_bfloat16*)a.p)[i]) : __ldg((const float*)a.p + i);
+}
+
+// Chunk prefix of the current segment table (thread 0), then sync.
+__device__ void build_chunks(ClShared& s) {
+  if (threadIdx.x == 0) {
+    int c = 0;
+    for (int i = 0; i < s.nseg; ++i) {
+      s.seg_chunk0[i] = c;
+      if (s.seg_on[i]) c += (s.seg_count[i] + CH - 1) / CH;
+    }
+    s.seg_chunk0[s.nseg] = c;
+    s.nchunks = c;
+  }
+  __syncthreads();
+}
+
+// Double-float value hi + lo.  Sums run in FP32 pairs: FP64 issues at 1/64 of
+// the FP32 rate on this GPU, so warp-wide FP64 reductions would dominate.
+struct F2 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+  const float s = a.hi + b.hi;                      // TwoSum of the high parts
+  const float bp = s - a.hi;
+  float e = (a.hi - (s - bp)) + (b.hi - bp);
+  e += a.lo + b.lo;
+  F2 r;
+  r.hi = s + e;                                     // FastTwoSum renormalisation
+  r.lo = e - (r.hi - s);
+  return r;
+}
+
+__device__ __forceinline__ double f2_to_d(F2 x) { return (double)x.hi + (double)x.lo; }
+
+struct ArgMax {
+  double d;
+  int i;
+};
+
+__device__ __forceinline__ F2 shfl_xor_t(F2 x, int o) {
+  F2 r;
+  r.hi = __shfl_xor_sync(0xffffffffu, x.hi, o);
+  r.lo = __shfl_xor_sync(0xffffffffu, x.lo, o);
+  return r;
+}
+__device__ __forceinline__ double shfl_xor_t(double x, int o) { return __shfl_xor_sync(0xffffffffu, x, o); }
+__device__ __forceinline__ float shfl_xor_t(float x, int o) { return __shfl_xor_sync(0xffffffffu, x, o); }
+__device__ __forceinline__ ArgMax shfl_xor_t(ArgMax x, int o) {
+  ArgMax r;
+  r.d = __shfl_xor_sync(0xffffffffu, x.d, o);
+  r.i = __shfl_xor_sync(0xffffffffu, x.i, o);
+  return r;
+}
+
+// Side of the accepted 2-means assignment at position pos; rv = 1 + the
+// iteration whose changes were undone (0: none).
+__device__ __forceinline__ int accepted_side(const ClArgs& a, int pos, int rv) {
+  const int sd = (int)__ldcg(a.side + pos);
+  return (rv > 0 && (int)__ldcg(a.side + a.N + pos) == rv) ? sd ^ 1 : sd;
+}
+
+// x / y in FP64 from the correctly rounded reciprocal (__drcp_rn) and one
+// remainder correction (Markstein's FMA refinement: e = x - q y exactly,
+// q += e / y); exact when the quotient is representable, as for the mean of
+// identical points.  Cheaper than the FP64 division sequence.
+__device__ __forceinline__ double quotient(double x, double y) {
+  const double r = __drcp_rn(y);
+  double q = x * r;
+  const double e = fma(-q, y, x);
+  return fma(e, r, q);
+}
+
+// Deterministic replay of a cross-block reduction, run identically by every
+// block: for each value v, lane l of a warp combines the contributors
+// i = l, l + 32, ... of v, and the lanes are combined by a fixed xor tree.
+// The loads of IPW values per warp are independent, so their latencies
+// overlap.  combine(a, b) must be commutative; init is its identity.
+template <int IPW, class T, class NC, class SRC, class COMB, class DST>
+__device__ void replay(int nvals, T init, NC nc_of, SRC src, COMB combine, DST dst) {
+  constexpr int SMALL = 8;   // at most this many contributors: one thread per value
+  for (int v = threadIdx.x; v < nvals; v += CL_THREADS) {
+    const int n = nc_of(v);
+    if (n > SMALL) continue;
+    T buf[SMALL];
+#pragma unroll
+    for (int i = 0; i < SMALL; ++i) buf[i] = (i < n) ? src(v, i) : init;
+    T acc = init;
+#pragma unroll
+    for (int i = 0; i < SMALL; ++i) acc = combine(acc, buf[i]);
+    dst(v, acc);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int base = warp * IPW; base < nvals; base += CL_WARPS * IPW) {
+    T part[IPW];
+    bool big[IPW];
+#pragma unroll
+    for (int k = 0; k < IPW; ++k) {
+      part[k] = init;
+      const int v = base + k;
+      const int n = v < nvals ? nc_of(v) : 0;
+      big[k] = n > SMALL;
+      if (big[k]) {
+#pragma unroll 4
+        for (int i = lane; i < n; i += 32) part[k] = combine(part[k], src(v, i));
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < IPW; ++k) {
+      if (!big[k]) continue;
+      T x = part[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x = combine(x, shfl_xor_t(x, o));
+      if (lane == 0) dst(base + k, x);
+    }
+  }
+}
+
+// Iterate over this block's chunks at chunk granularity: f(seg, base, end, j)
+// with the chunk's positions base + u * CL_THREADS + tid (u < PPT), < end;
+// flush(seg) once per segment after its last chunk in this block.
+template <class F, class Flush>
+__device__ void for_blocks(const ClArgs& a, const ClShared& s, F f, Flush flush) {
+  int cur = -1, seg = 0;
+  for (int j = blockIdx.x; j < s.nchunks; j += a.G) {
+    while (s.seg_chunk0[seg + 1] <= j) ++seg;
+    if (seg != cur) {
+      if (cur >= 0) flush(cur);
+      cur = seg;
+    }
+    const int base = s.seg_start[seg] + (j - s.seg_chunk0[seg]) * CH;
+    f(seg, base, s.seg_start[seg] + s.seg_count[seg], j);
+  }
+  if (cur >= 0) flush(cur);
+}
+
+// Blocks whose partial results cover segment `seg`, in a fixed order.
+__device__ __forceinline__ int contrib_count(const ClArgs& a, const ClShared& s, int seg) {
+  const int nch = s.seg_chunk0[seg + 1] - s.seg_chunk0[seg];
+  return nch < a.G ? nch : a.G;
+}
+__device__ __forceinline__ int contrib_block(const ClArgs& a, const ClShared& s, int seg, int i) {
+  return (s.seg_chunk0[seg] + i) % a.G;
+}
+
+// hi + x = t + e exactly (Knuth's TwoSum); the error terms are summed in lo.
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+  const float t = hi + x;
+  const float bp = t - hi;
+  const float e = (hi - (t - bp)) + (x - bp);
+  hi = t;
+  lo += e;
+}
+
+// Block sum of NV per-thread double-float values, fixed order.  Within a warp
+// the values are reduced by recursive halving (each lane keeps half of its
+// values and adds its partner's copy of them), so a warp needs NV - 1 pair
+// additions per lane instead of 5 NV; lane l ends with value (l >> (5-L)) & (NV-1)
+// (L = log2 NV <= 5).  The warp results are then added across warps.  out
+// receives nv pairs (hi, lo).
+template <int NV>
+__device__ void block_sum_f2(const float (&hi)[NV], const float (&lo)[NV], int nv, ClShared& s,
+                             float* out) {
+  static_assert((NV & (NV - 1)) == 0, "power of two");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int H = NV > 32 ? NV / 32 : 1;          // values per lane after the halving
+  constexpr int NV1 = NV > 32 ? 32 : NV;            // values per group of the halving
+#pragma unroll
+  for (int h = 0; h < H; ++h) {
+    F2 v[NV1];
+#pragma unroll
+    for (int i = 0; i < NV1; ++i) {
+      v[i].hi = hi[h * NV1 + i];
+      v[i].lo = lo[h * NV1 + i];
+    }
+    int n = NV1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      if (n > 1) {
+        const int half = n / 2;
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < NV1 / 2; ++i) {
+          if (i < half) {
+            const F2 send = up ? v[i] : v[i + half];
+            const F2 keep = up ? v[i + half] : v[i];
+            v[i] = f2_add(keep, shfl_xor_t(send, o));
+          }
+        }
+        n = half;
+      } else {
+        v[0] = f2_add(v[0], shfl_xor_t(v[0], o));
+      }
+    }
+    constexpr int L = NV1 == 32 ? 5 : NV1 == 16 ? 4 : NV1 == 8 ? 3 : NV1 == 4 ? 2 : NV1 == 2 ? 1 : 0;
+    const int idx = h * NV1 + ((lane >> (5 - L)) & (NV1 - 1));
+    if ((lane & ((1 << (5 - L)) - 1)) == 0) {
+      s.redg[warp][2 * idx] = v[0].hi;
+      s.redg[warp][2 * idx + 1] = v[0].lo;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nv; i += CL_THREADS) {
+    F2 t;
+    t.hi = s.redg[0][2 * i];
+    t.lo = s.redg[0][2 * i + 1];
+#pragma unroll
+    for (int w = 1; w < CL_WARPS; ++w) {
+      F2 u;
+      u.hi = s.redg[w][2 * i];
+      u.lo = s.redg[w][2 * i + 1];
+      t = f2_add(t, u);
+    }
+    out[2 * i] = t.hi;
+    out[2 * i + 1] = t.lo;
+  }
+  __syncthreads();
+}
+
+__device__ void block_sum_i2(int v0, int v1, ClShared& s, int* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+    v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+  }
+  if (lane == 0) { s.redi[warp][0] = v0; s.redi[warp][1] = v1; }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    int t = 0;
+    for (int w = 0; w < CL_WARPS; ++w) t += s.redi[w][threadIdx.x];
+    out[threadIdx.x] = t;
+  }
+  __syncthreads();
+}
+
+// Exclusive scan of one int per thread across the block; *total = sum.
+__device__ int block_excl_scan(int v, ClShared& s, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s.scanw[warp] = x;
+  __syncthreads();
+  int before = 0, t = 0;
+#pragma unroll
+  for (int w = 0; w < CL_WARPS; ++w) {
+    if (w < warp) before += s.scanw[w];
+    t += s.scanw[w];
+  }
+  __syncthreads();
+  *total = t;
+  return before + x - v;
+}
+
+// Block max of a float and sum of a float; results written by thread 0.
+__device__ void block_max_sum(float m, F2 sum, ClShared& s, float* out_max, float* out_sum) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    sum = f2_add(sum, shfl_xor_t(sum, o));
+  }
+  if (lane == 0) { s.redd[warp] = m; s.redg[warp][0] = sum.hi; s.redg[warp][1] = sum.lo; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float mm = s.redd[0];
+    F2 ss;
+    ss.hi = s.redg[0][0];
+    ss.lo = s.redg[0][1];
+    for (int w = 1; w < CL_WARPS; ++w) {
+      F2 u;
+      u.hi = s.redg[w][0];
+      u.lo = s.redg[w][1];
+      mm = fmaxf(mm, s.redd[w]);
+      ss = f2_add(ss, u);
+    }
+    *out_max = mm;
+    out_sum[0] = ss.hi;
+    out_sum[1] = ss.lo;
+  }
+  __syncthreads();
+}
+
+__device__ void block_argmax(double d, int idx, ClShared& s, double* out_d, int* out_i) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double d2 = __shfl_xor_sync(0xffffffffu, d, o);
+    const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (better(d2, i2, d, idx)) { d = d2; idx = i2; }
+  }
+  if (lane == 0) { s.redD[warp] = d; s.redx[warp] = idx; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double bd = s.redD[0];
+    int bi = s.redx[0];
+    for (int w = 1; w < CL_WARPS; ++w)
+      if (better(s.redD[w], s.redx[w], bd, bi)) { bd = s.redD[w]; bi = s.redx[w]; }
+    *out_d = bd;
+    *out_i = bi;
+  }
+  __syncthreads();
+}
+
+// Coordinate d of the point at permutation position pos.
+__device__ __forceinline__ float xat(const ClArgs& a, int d, int pos) {
+  return __ldcg(a.X + (size_t)d * a.N + pos);
+}
+
+// Replay of the sequential greedy rule on the known tree (warp 0).  Leaves
+// carry their cluster index; the leaf of largest SSE (ties -> lowest
+// cluster index) is split next.  A leaf whose split is not known yet is
+// recorded as needed, removed, and counted as split, and the replay goes on.
+__device__ void simulate(ClShared& s, int K, int maxneeded) {
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  if (lane == 0) {
+    s.leaf_node[0] = 0;
+    s.leaf_cl[0] = 0;
+    s.nleaves = 1;
+    s.nclusters = 1;
+    s.nneeded = 0;
+  }
+  __syncwarp();
+  while (true) {
+    const int nl = s.nleaves;
+    if (s.nclusters >= K || nl == 0 || s.nneeded >= maxneeded) break;
+    double bd = -1.0;
+    int bc = 0x7fffffff, bl = -1;
+    for (int i = lane; i < nl; i += 32) {
+      const double v = s.sim_sse[s.leaf_node[i]];
+      const int c = s.leaf_cl[i];
+      if (v > bd || (v == bd && c < bc)) { bd = v; bc = c; bl = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double v2 = __shfl_xor_sync(0xffffffffu, bd, o);
+      const int c2 = __shfl_xor_sync(0xffffffffu, bc, o);
+      const int l2 = __shfl_xor_sync(0xffffffffu, bl, o);
+      if (v2 > bd || (v2 == bd && c2 < bc)) { bd = v2; bc = c2; bl = l2; }
+    }
+    if (!(bd > 0.0)) break;
+    if (lane == 0) {
+      const int nd = s.leaf_node[bl];
+      const int c0 = s.sim_child0[nd];
+      if (c0 >= 0) {
+        s.leaf_node[bl] = c0;
+        s.leaf_node[nl] = c0 + 1;
+        s.leaf_cl[nl] = s.nclusters;
+        s.nleaves = nl + 1;
+      } else {
+        s.needed[s.nneeded++] = nd;
+        s.leaf_node[bl] = s.leaf_node[nl - 1];
+        s.leaf_cl[bl] = s.leaf_cl[nl - 1];
+        s.nleaves = nl - 1;
+      }
+      s.nclusters += 1;
+    }
+    __syncwarp();
+  }
+}
+
+__host__ __device__ constexpr size_t dyn_c64_offset(int rho) {
+  return ((sizeof(float) * MAXSEG * (size_t)rho + 15) / 16) * 16;
+}
+
+__host__ __device__ constexpr size_t dyn_smem_bytes(int rho) {
+  return dyn_c64_offset(rho) + sizeof(double) * ((size_t)MAXSEG * rho + (size_t)MAXACT * (rho + 2) +
+                                                 3 * (size_t)MAXACT * rho);
+}
+
+template <int RMAX>
+__global__ void __launch_bounds__(CL_THREADS, 1)
+cluster_kernel(const ClArgs a) {
+  __shared__ ClShared s;
+  extern __shared__ __align__(16) unsigned char dyn[];
+  const int rho = a.rho;
+  const int PS = 2 * (rho + 1);   // floats per partial record (pairs)
+  float* c32 = (float*)dyn;                                   // MAXSEG x rho
+  double* c64 = (double*)(dyn + dyn_c64_offset(rho));         // MAXSEG x rho
+  double* tmp = c64 + MAXSEG * rho;                           // MAXACT x (rho + 2)
+  double* acc_sum = tmp + MAXACT * (rho + 2);                 // MAXACT x rho
+  double* nsum = acc_sum + MAXACT * rho;                      // MAXACT x rho sums of the split nodes
+  double* mean_a = nsum + MAXACT * rho;                       // MAXACT x rho
+  auto acc_sum_a = [&](int i, int d) -> double& { return mean_a[i * rho + d]; };
+  unsigned gen = 0;
+  const int tid = threadIdx.x, bid = blockIdx.x;
+  const size_t N = (size_t)a.N;
+  int nnodes = 1, rounds = 0, lloyd_max = 0;
+  // points whose coordinates are loaded together (registers permitting)
+  constexpr int UB = RMAX <= 4 ? 8 : (RMAX <= 8 ? 4 : (RMAX <= 32 ? 2 : 1));
+  static_assert(PPT % UB == 0, "load batch must divide the points per thread");
+
+  // ------------------------------------------------------------ root node
+  if (tid == 0) {
+    s.nseg = 1;
+    s.seg_start[0] = 0;
+    s.seg_count[0] = a.N;
+    s.seg_on[0] = 1;
+  }
+  __syncthreads();
+  build_chunks(s);
+  {
+    float hi[RMAX], lo[RMAX];
+#pragma unroll
+    for (int d = 0; d < RMAX; ++d) hi[d] = lo[d] = 0.0f;
+    for_blocks(a, s,
+        [&](int, int base, int end, int) {
+#pragma unroll
+          for (int u0 = 0; u0 < PPT; u0 += UB) {
+            float x[UB][RMAX];
+#pragma unroll
+            for (int b = 0; b < UB; ++b) {
+              const int pos = base + (u0 + b) * CL_THREADS + tid;
+#pragma unroll
+              for (int d = 0; d < RMAX; ++d)
+                x[b][d] = (pos < end && d < rho) ? guide_at(a, (size_t)d * N + pos) : 0.0f;
+            }
+#pragma unroll
+            for (int b = 0; b < UB; ++b) {
+              const int pos = base + (u0 + b) * CL_THREADS + tid;
+              if (pos >= end) continue;
+              a.perm[pos] = (uint32_t)pos;
+#pragma unroll
+              for (int d = 0; d < RMAX; ++d) {
+                if (d < rho) {
+                  a.X[(size_t)d * N + pos] = x[b][d];
+                  two_sum_acc(hi[d], lo[d], x[b][d]);
+                }
+              }
+            }
+          }
+        },
+        [&](int seg) {
+          block_sum_f2<RMAX>(hi, lo, rho, s, a.pf + ((size_t)bid * MAXSEG + seg) * PS);
+#pragma unroll
+          for (int d = 0; d < RMAX; ++d) hi[d] = lo[d] = 0.0f;
+        });
+  }
+  if (!grid_barrier(a, gen, s, TR_ROOT)) return;
+  replay<8>(rho, F2{0.0f, 0.0f}, [&](int) { return contrib_count(a, s, 0); },
+      [&](int d, int i) {
+        const float* q = a.pf + ((size_t)contrib_block(a, s, 0, i) * MAXSEG) * PS + 2 * d;
+        return F2{__ldcg(q), __ldcg(q + 1)};
+      },
+      [](F2 x, F2 y) { return f2_add(x, y); },
+      [&](int d, F2 tf) {
+        const double t = f2_to_d(tf);
+        const double m = t / (double)a.N;
+        c64[d] = m;
+        c32[d] = (float)m;
+        if (bid == 0) a.node_sum[d] = t;
+      });
+  __syncthreads();
+
+  // Distance statistics of every segment of the table against the centres
+  // c32[seg] / c64[seg]: SSE, then the farthest point decided in FP64 among
+  // the FP32 candidates (ties -> lowest raster index).  `from_scratch` reads
+  // the points (and raster indices) from the scatter buffers and moves them
+  // into place.  Results in s.segmax / s.segsse / s.segarg.  Two barriers.
+  auto dist_stats = [&](bool from_scratch) -> bool {
+    {
+      float mx = -1.0f;
+      F2 sse{0.0f, 0.0f};
+      for_blocks(a, s,
+          [&](int seg, int base, int end, int) {
+            const float* c = c32 + seg * rho;
+#pragma unroll
+            for (int u0 = 0; u0 < PPT; u0 += UB) {
+              float x[UB][RMAX];
+              uint32_t pid[UB];
+#pragma unroll
+              for (int b = 0; b < UB; ++b) {
+                const int pos = base + (u0 + b) * CL_THREADS + tid;
+                const bool v = pos < end;
+                const float* src = from_scratch ? a.X2 : a.X;
+                pid[b] = (v && from_scratch) ? __ldcg(a.perm2 + pos) : 0u;
+#pragma unroll
+                for (int d = 0; d < RMAX; ++d)
+                  x[b][d] = (v && d < rho) ? __ldcg(src + (size_t)d * N + pos) : 0.0f;
+              }
+#pragma unroll
+              for (int b = 0; b < UB; ++b) {
+                const int pos = base + (u0 + b) * CL_THREADS + tid;
+                if (pos >= end) continue;
+                float d2 = 0.0f;
+#pragma unroll
+                for (int d = 0; d < RMAX; ++d) {
+                  if (d < rho) {
+                    if (from_scratch) a.X[(size_t)d * N + pos] = x[b][d];
+                    const float t = x[b][d] - c[d];
+                    d2 = fmaf(t, t, d2);
+                  }
+                }
+                if (from_scratch) a.perm[pos] = pid[b];
+                a.d32[pos] = d2;
+                mx = fmaxf(mx, d2);
+                two_sum_acc(sse.hi, sse.lo, d2);
+              }
+            }
+          },
+          [&](int seg) {
+            block_max_sum(mx, sse, s, a.pd + (size_t)bid * MAXSEG + seg,
+                          a.pf + ((size_t)bid * MAXSEG + seg) * PS);
+            mx = -1.0f;
+            sse = F2{0.0f, 0.0f};
+          });
+    }
+    if (!grid_barrier(a, gen, s, TR_DIST1)) return false;
+    {
+      auto ncf = [&](int seg) { return s.seg_on[seg] ? contrib_count(a, s, seg) : 0; };
+      auto off = [&](int seg, int i) { return (size_t)contrib_block(a, s, seg, i) * MAXSEG + seg; };
+      replay<8>(s.nseg, -1.0f, ncf, [&](int seg, int i) { return __ldcg(a.pd + off(seg, i)); },
+          [](float x, float y) { return fmaxf(x, y); }, [&](int seg, float m) { s.segmax[seg] = m; });
+      replay<8>(s.nseg, F2{0.0f, 0.0f}, ncf,
+          [&](int seg, int i) {
+            const float* q = a.pf + off(seg, i) * PS;
+            return F2{__ldcg(q), __ldcg(q + 1)};
+          },
+          [](F2 x, F2 y) { return f2_add(x, y); }, [&](int seg, F2 t) { s.segsse[seg] = f2_to_d(t); });
+    }
+    __syncthreads();
+    {
+      double bd = -1.0;
+      int bi = 0x7fffffff;
+      for_blocks(a, s,
+          [&](int seg, int base, int end, int) {
+            const float m = s.segmax[seg];
+            float dd[PPT];
+#pragma unroll
+            for (int u = 0; u < PPT; ++u) {
+              const int pos = base + u * CL_THREADS + tid;
+              dd[u] = (pos < end) ? __ldcg(a.d32 + pos) : -1.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < PPT; ++u) {
+              const int pos = base + u * CL_THREADS + tid;
+              if (pos >= end) continue;
+              if (m > 0.0f && dd[u] < m * (1.0f - CAND_REL)) continue;
+              const int idx = (int)__ldcg(a.perm + pos);
+              double e = 0.0;
+              if (m > 0.0f) {
+                const double* c = c64 + (size_t)seg * rho;
+                float xv[RMAX];
+#pragma unroll
+                for (int d = 0; d < RMAX; ++d) xv[d] = (d < rho) ? xat(a, d, pos) : 0.0f;
+#pragma unroll
+                for (int d = 0; d < RMAX; ++d) {
+                  if (d < rho) {
+                    const double t = (double)xv[d] - c[d];
+                    e = fma(t, t, e);
+                  }
+                }
+              }
+              if (better(e, idx, bd, bi)) { bd = e; bi = idx; }
+            }
+          },
+          [&](int seg) {
+            block_argmax(bd, bi, s, a.pdd + (size_t)bid * MAXSEG + seg,
+                         a.px + (size_t)bid * MAXSEG + seg);
+            bd = -1.0;
+            bi = 0x7fffffff;
+          });
+    }
+    if (!grid_barrier(a, gen, s, TR_DIST2)) return false;
+    {
+      ArgMax none;
+      none.d = -1.0;
+      none.i = 0x7fffffff;
+      replay<8>(s.nseg, none, [&](int seg) { return s.seg_on[seg] ? contrib_count(a, s, seg) : 0; },
+          [&](int seg, int i) {
+            const size_t off = (size_t)contrib_block(a, s, seg, i) * MAXSEG + seg;
+            ArgMax r;
+            r.d = __ldcg(a.pdd + off);
+            r.i = __ldcg(a.px + off);
+            return r;
+          },
+          [](ArgMax x, ArgMax y) { return better(y.d, y.i, x.d, x.i) ? y : x; },
+          [&](int seg, ArgMax r) { s.segarg[seg] = r.i; });
+    }
+    __syncthreads();
+    return true;
+  };
+
+  if (!dist_stats(false)) return;
+  if (bid == 0 && tid == 0) {
+    NodeRec r;
+    r.start = 0;
+    r.count = a.N;
+    r.child0 = -1;
+    r.far_idx = s.segarg[0];
+    r.sse = s.segsse[0];
+    a.nodes[0] = r;
+  }
+  if (!grid_barrier(a, gen, s, TR_NODE)) return;
+
+  // ------------------------------------------------------------ rounds
+  while (true) {
+    for (int i = tid; i < nnodes; i += CL_THREADS) {
+      s.sim_sse[i] = __ldcg(&a.nodes[i].sse);
+      s.sim_child0[i] = __ldcg(&a.nodes[i].child0);
+    }
+    __syncthreads();
+    int room = (MAXNODES - nnodes) / 2;
+    if (room > MAXACT) room = MAXACT;
+    simulate(s, a.K, room);
+    __syncthreads();
+    if (s.nneeded == 0) break;
+    if (room == 0) {                       // node table full: cannot go on
+      if (bid == 0 && tid == 0) record_error(a.ctrl, HDF_EUNSUPPORTED);
+      return;
+    }
+    ++rounds;
+    // ---- slots, and the point farthest from a (segments = slots)
+    if (tid == 0) {
+      s.nslots = s.nneeded;
+      s.nseg = s.nneeded;
+      for (int i = 0; i < s.nneeded; ++i) {
+        const int nd = s.needed[i];
+        SlotRec& sl = s.slot[i];
+        sl.node = nd;
+        sl.start = __ldcg(&a.nodes[nd].start);
+        sl.count = __ldcg(&a.nodes[nd].count);
+        sl.a_idx = __ldcg(&a.nodes[nd].far_idx);
+        sl.b_idx = -1;
+        sl.done = 0;
+        sl.iters = 0;
+        sl.rev_it = -1;
+        sl.cnt_b_cur = 0;
+        sl.cnt_b_acc = 0;
+        sl.split = 1;
+        sl.recompute = 0;
+        s.seg_start[i] = sl.start;
+        s.seg_count[i] = sl.count;
+        s.seg_on[i] = 1;
+      }
+    }
+    __syncthreads();
+    build_chunks(s);
+    for (int v = tid; v < s.nslots * rho; v += CL_THREADS) {
+      const int sl = v / rho, d = v % rho;
+      const float x = guide_at(a, (size_t)d * N + s.slot[sl].a_idx);
+      c32[sl * rho + d] = x;
+      c64[sl * rho + d] = (double)x;
+      nsum[v] = __ldcg(a.node_sum + (size_t)s.slot[sl].node * rho + d);
+    }
+    __syncthreads();
+    if (!dist_stats(false)) return;
+    if (tid == 0) {
+      for (int i = 0; i < s.nslots; ++i) {
+        SlotRec& sl = s.slot[i];
+        sl.b_idx = s.segarg[i];
+        if (!(s.segmax[i] > 0.0f) || sl.b_idx < 0 || sl.b_idx >= a.N) {   // all points coincide
+          sl.split = 0;
+          sl.done = 1;
+          sl.b_idx = sl.a_idx;
+        }
+      }
+    }
+    __syncthreads();
+    // centres a, b of split i at [2i], [2i + 1]
+    for (int v = tid; v < s.nslots * 2 * rho; v += CL_THREADS) {
+      const int sl = v / (2 * rho), w = (v / rho) % 2, d = v % rho;
+      const int idx = w == 0 ? s.slot[sl].a_idx : s.slot[sl].b_idx;
+      c64[(2 * sl + w) * rho + d] = (double)guide_at(a, (size_t)d * N + idx);
+    }
+    __syncthreads();
+    for (int v = tid; v < s.nslots * 2 * rho; v += CL_THREADS) c32[v] = (float)c64[v];
+    if (tid < s.nslots) s.seg_on[tid] = !s.slot[tid].done;
+    __syncthreads();
+    for (int i = tid >> 5; i < s.nslots; i += CL_WARPS) {     // |c_a| + |c_b| per split
+      double na = 0.0, nb = 0.0;
+      for (int d = tid & 31; d < rho; d += 32) {
+        na += c64[(2 * i) * rho + d] * c64[(2 * i) * rho + d];
+        nb += c64[(2 * i + 1) * rho + d] * c64[(2 * i + 1) * rho + d];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        na += __shfl_xor_sync(0xffffffffu, na, o);
+        nb += __shfl_xor_sync(0xffffffffu, nb, o);
+      }
+      if ((tid & 31) == 0) {
+        s.cabs[i] = (float)((sqrt(na) + sqrt(nb)) * (1.0 / 1048576.0));
+        s.slack[i] = 0.0f;
+        s.cum[i] = 0.0;
+      }
+    }
+    __syncthreads();
+    build_chunks(s);
+
+    // ---- Lloyd iterations, all splits of the round together
+    for (int it = 0; it < MAX_LLOYD; ++it) {
+      const int all_done = __syncthreads_and(tid < s.nslots ? s.slot[tid].done : 1);
+      if (all_done) break;
+      {
+        // it == 0: full side-b sums; it > 0: change of the side-b sums (points
+        // that switched), so that skipped points need no coordinates at all.
+        float hi[RMAX], lo[RMAX];
+        int cnt = 0, chg = 0;
+#pragma unroll
+        for (int d = 0; d < RMAX; ++d) hi[d] = lo[d] = 0.0f;
+        for_blocks(a, s,
+            [&](int seg, int base, int end, int) {
+              // fast path: the assignment cannot change while the margin bound
+              // (stored margin minus the centre movement since) is positive
+              const float cum = (float)s.cum[seg];
+              bool heavy[PPT];
+#pragma unroll
+              for (int u = 0; u < PPT; ++u) {
+                const int pos = base + u * CL_THREADS + tid;
+                const float m0 = (pos < end && it > 0) ? __ldcg(a.marg + pos) : -1.0f;
+                heavy[u] = pos < end && !(m0 - cum > 1e-6f * (fabsf(m0) + cum));
+              }
+              // compact the chunk's heavy points and spread them over the block
+              int nh = 0;
+#pragma unroll
+              for (int u = 0; u < PPT; ++u) nh += heavy[u];
+              int nheavy;
+              int k = block_excl_scan(nh, s, &nheavy);
+#pragma unroll
+              for (int u = 0; u < PPT; ++u)
+                if (heavy[u]) s.hlist[k++] = base + u * CL_THREADS + tid;
+              __syncthreads();
+              const float* ca = c32 + (2 * seg) * rho;
+              const float* cb = ca + rho;
+              for (int q0 = 0; q0 < nheavy; q0 += UB * CL_THREADS) {
+                int hp[UB];
+                float x[UB][RMAX];
+#pragma unroll
+                for (int b = 0; b < UB; ++b) {
+                  const int q = q0 + b * CL_THREADS + tid;
+                  hp[b] = q < nheavy ? s.hlist[q] : -1;
+#pragma unroll
+                  for (int d = 0; d < RMAX; ++d)
+                    x[b][d] = (hp[b] >= 0 && d < rho) ? xat(a, d, hp[b]) : 0.0f;
+                }
+#pragma unroll
+                for (int b = 0; b < UB; ++b) {
+                  if (hp[b] < 0) continue;
+                  const int pos = hp[b];
+                  float da = 0.0f, db = 0.0f;
+#pragma unroll
+                  for (int d = 0; d < RMAX; ++d) {
+                    if (d < rho) {
+                      const float ta = x[b][d] - ca[d], tb = x[b][d] - cb[d];
+                      da = fmaf(ta, ta, da);
+                      db = fmaf(tb, tb, db);
+                    }
+                  }
+                  bool sd = db < da;
+                  if (fabsf(da - db) <= TIE_REL * (da + db)) {
+                    const double* ea = c64 + (2 * seg) * rho;
+                    const double* eb = ea + rho;
+                    double e_a = 0.0, e_b = 0.0;
+#pragma unroll
+                    for (int d = 0; d < RMAX; ++d) {
+                      if (d < rho) {
+                        const double xd = (double)x[b][d];
+                        e_a = fma(xd - ea[d], xd - ea[d], e_a);
+                        e_b = fma(xd - eb[d], xd - eb[d], e_b);
+                      }
+                    }
+                    sd = e_b < e_a;
+                  }
+                  const float ra = sqrtf(da), rb = sqrtf(db);
+                  a.marg[pos] = fabsf(rb - ra) - MARGIN_REL * (ra + rb) - s.cabs[seg] + cum;
+                  const int sdp = (it > 0) ? (int)__ldcg(a.side + pos) : -1;
+                  if ((int)sd != sdp) {
+                    a.side[pos] = (uint8_t)sd;
+                    a.side[N + pos] = (uint8_t)(it + 1);   // iteration of the last change
+                  }
+                  if (it == 0) {
+                    if (sd) {
+                      ++cnt;
+#pragma unroll
+                      for (int d = 0; d < RMAX; ++d)
+                        if (d < rho) two_sum_acc(hi[d], lo[d], x[b][d]);
+                    }
+                  } else if ((int)sd != sdp) {
+                    ++chg;
+                    cnt += sd ? 1 : -1;
+#pragma unroll
+                    for (int d = 0; d < RMAX; ++d)
+                      if (d < rho) two_sum_acc(hi[d], lo[d], sd ? x[b][d] : -x[b][d]);
+                  }
+                }
+              }
+              __syncthreads();   // hlist is reused by the next chunk
+            },
+            [&](int seg) {
+              const size_t off = (size_t)bid * MAXSEG + seg;
+              block_sum_f2<RMAX>(hi, lo, rho, s, a.pf + off * PS);
+              block_sum_i2(cnt, chg, s, a.pi + off * 2);
+#pragma unroll
+              for (int d = 0; d < RMAX; ++d) hi[d] = lo[d] = 0.0f;
+              cnt = 0;
+              chg = 0;
+            });
+      }
+      trace_event(a.trace, TR_LPASS);
+      if (!grid_barrier(a, gen, s, TR_LLOYD)) return;
+      // replay the reduction of every active split: side-b sums, count, changes
+      // Each split's partial sums are reduced by its owner block (split i ->
+      // block i mod G) in a fixed order and published; one more barrier, then
+      // every block reads the published values.
+      for (int sl = bid; sl < s.nslots; sl += a.G) {
+        if (s.slot[sl].done) continue;
+        const int nc = contrib_count(a, s, sl);
+        const int lane = tid & 31, warp = tid >> 5;
+        for (int d0 = warp; d0 < rho + 2; d0 += CL_WARPS) {
+          F2 t{0.0f, 0.0f};
+          for (int i = lane; i < nc; i += 32) {
+            const size_t off = (size_t)contrib_block(a, s, sl, i) * MAXSEG + sl;
+            const F2 v = d0 < rho ? F2{__ldcg(a.pf + off * PS + 2 * d0), __ldcg(a.pf + off * PS + 2 * d0 + 1)}
+                                  : F2{(float)__ldcg(a.pi + off * 2 + (d0 - rho)), 0.0f};
+            t = f2_add(t, v);
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) t = f2_add(t, shfl_xor_t(t, o));
+          if (lane == 0) a.fin[sl * (rho + 2) + d0] = f2_to_d(t);
+        }
+      }
+      if (!grid_barrier(a, gen, s, TR_LPUB)) return;
+      for (int v = tid; v < s.nslots * (rho + 2); v += CL_THREADS)
+        tmp[v] = s.slot[v / (rho + 2)].done ? 0.0 : __ldcg(a.fin + v);
+      __syncthreads();
+      trace_event(a.trace, TR_LREPLAY);
+      for (int i = tid; i < s.nslots; i += CL_THREADS) {
+        {
+          SlotRec& sl = s.slot[i];
+          sl.recompute = 0;
+          if (sl.done) continue;
+          const int cb = (it == 0 ? 0 : sl.cnt_b_acc) + (int)tmp[i * (rho + 2) + rho];
+          const int changed = (int)tmp[i * (rho + 2) + rho + 1];
+          if (it == 0 && (cb == 0 || cb == sl.count)) {   // degenerate pair: not splittable
+            sl.done = 1;
+            sl.split = 0;
+            continue;
+          }
+          if (it > 0 && (cb == 0 || cb == sl.count)) {   // a side would be empty:
+            sl.done = 1;                                    // keep the previous assignment
+            sl.rev_it = it;
+            sl.iters = it;
+            continue;
+          }
+          if (it > 0 && changed == 0) {                    // converged
+            sl.done = 1;
+            sl.iters = it;
+            continue;
+          }
+                                                            // accept this assignment
+          sl.cnt_b_cur = cb;
+          sl.iters = it + 1;
+          sl.recompute = 1;
+          if (it + 1 == MAX_LLOYD) sl.done = 1;
+        }
+      }
+      __syncthreads();
+      // accepted sums and the new centres (means of the two sides); the distance
+      // each centre moved bounds the change of every stored margin
+      for (int v = tid; v < s.nslots * rho; v += CL_THREADS) {
+        const int i = v / rho, d = v % rho;
+        if (s.slot[i].recompute && it > 0) tmp[i * (rho + 2) + d] += acc_sum[i * rho + d];
+      }
+      __syncthreads();
+      // new means (stored in tmp) and the distance each centre moved
+      for (int v = tid; v < s.nslots * rho; v += CL_THREADS) {
+        const int i = v / rho, d = v % rho;
+        const SlotRec& sl = s.slot[i];
+        if (!sl.recompute) continue;
+        const double sb = tmp[i * (rho + 2) + d];
+        acc_sum[i * rho + d] = sb;
+        tmp[i * (rho + 2) + d] = quotient(sb, (double)sl.cnt_b_cur);                        // mean b
+        acc_sum_a(i, d) = quotient(nsum[i * rho + d] - sb, (double)(sl.count - sl.cnt_b_cur));  // mean a
+      }
+      __syncthreads();
+      for (int i = tid >> 5; i < s.nslots; i += CL_WARPS) {
+        const SlotRec& sl = s.slot[i];
+        if (!sl.recompute) continue;
+        double ma2 = 0.0, mb2 = 0.0, na = 0.0, nb = 0.0;
+        for (int d = tid & 31; d < rho; d += 32) {
+          const double ma = acc_sum_a(i, d), mb = tmp[i * (rho + 2) + d];
+          const double ua = ma - c64[(2 * i) * rho + d], ub = mb - c64[(2 * i + 1) * rho + d];
+          ma2 += ua * ua;
+          mb2 += ub * ub;
+          na += ma * ma;
+          nb += mb * mb;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          ma2 += __shfl_xor_sync(0xffffffffu, ma2, o);
+          mb2 += __shfl_xor_sync(0xffffffffu, mb2, o);
+          na += __shfl_xor_sync(0xffffffffu, na, o);
+          nb += __shfl_xor_sync(0xffffffffu, nb, o);
+        }
+        if ((tid & 31) == 0) {
+          s.slack[i] = (float)((sqrt(ma2) + sqrt(mb2)) * ROUND_UP) + 1e-30f;
+          s.cum[i] = (s.cum[i] + (double)s.slack[i]) * ROUND_UP;
+          s.cabs[i] = (float)((sqrt(na) + sqrt(nb)) * (1.0 / 1048576.0));
+        }
+      }
+      __syncthreads();
+      for (int v = tid; v < s.nslots * rho; v += CL_THREADS) {
+        const int i = v / rho, d = v % rho;
+        if (!s.slot[i].recompute) continue;
+        const double ma = acc_sum_a(i, d), mb = tmp[i * (rho + 2) + d];
+        c64[(2 * i) * rho + d] = ma;
+        c64[(2 * i + 1) * rho + d] = mb;
+        c32[(2 * i) * rho + d] = (float)ma;
+        c32[(2 * i + 1) * rho + d] = (float)mb;
+      }
+      __syncthreads();
+      for (int i = tid; i < s.nslots; i += CL_THREADS) {
+        if (s.slot[i].recompute) s.slot[i].cnt_b_acc = s.slot[i].cnt_b_cur;
+        s.seg_on[i] = !s.slot[i].done;
+      }
+      __syncthreads();
+      build_chunks(s);
+      trace_event(a.trace, TR_LUPDATE);
+    }
+    if (tid == 0) {
+      for (int i = 0; i < s.nslots; ++i) {
+        if (s.slot[i].iters > lloyd_max) lloyd_max = s.slot[i].iters;
+        s.seg_on[i] = s.slot[i].split;
+      }
+    }
+    __syncthreads();
+    build_chunks(s);
+
+    // ---- stable partition of every split segment: side-a points first.
+    // Within a chunk thread t owns the PPT consecutive positions
+    // base + t*PPT + u, so one block-wide scan per chunk ranks the points.
+    auto chunk_geom = [&](int j, int& seg, int& base, int& end) {
+      while (s.seg_chunk0[seg + 1] <= j) ++seg;
+      base = s.seg_start[seg] + (j - s.seg_chunk0[seg]) * CH;
+      end = s.seg_start[seg] + s.seg_count[seg];
+    };
+    // exclusive block scan of v (one value per thread); also returns the total
+    auto block_scan = [&](int v, int& total) -> int {
+      const int lane = tid & 31, warp = tid >> 5;
+      int x = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) s.scanw[warp] = x;
+      __syncthreads();
+      int before = 0;
+      total = 0;
+#pragma unroll
+      for (int w = 0; w < CL_WARPS; ++w) {
+        if (w < warp) before += s.scanw[w];
+        total += s.scanw[w];
+      }
+      __syncthreads();
+      return before + x - v;
+    };
+    {
+      int seg = 0;
+      for (int j = bid; j < s.nchunks; j += a.G) {
+        int base, end;
+        chunk_geom(j, seg, base, end);
+        const int rv = s.slot[seg].rev_it + 1;   // 0: nothing undone
+        int c = 0;
+#pragma unroll
+        for (int u = 0; u < PPT; ++u) {
+          const int pos = base + tid * PPT + u;
+          if (pos < end) c += accepted_side(a, pos, rv);
+        }
+        int total;
+        block_scan(c, total);
+        if (tid == 0) a.chunk_cnt[j] = total;
+      }
+    }
+    if (!grid_barrier(a, gen, s, TR_COUNT)) return;
+    {
+      int seg = 0;
+      for (int j = bid; j < s.nchunks; j += a.G) {
+        int base, end;
+        chunk_geom(j, seg, base, end);
+        const SlotRec& sl = s.slot[seg];
+        const int rv = sl.rev_it + 1;
+        // side-b points in the earlier chunks of this segment
+        int pb = 0;
+        for (int q = s.seg_chunk0[seg] + tid; q < j; q += CL_THREADS) pb += __ldcg(a.chunk_cnt + q);
+        int before_b_chunk;
+        block_scan(pb, before_b_chunk);
+        int sdv[PPT], c = 0;
+#pragma unroll
+        for (int u = 0; u < PPT; ++u) {
+          const int pos = base + tid * PPT + u;
+          sdv[u] = (pos < end) ? accepted_side(a, pos, rv) : 0;
+          c += sdv[u];
+        }
+        int total;
+        int rank_b = before_b_chunk + block_scan(c, total);
+        const int cnt_a = sl.count - sl.cnt_b_acc;
+        int np[PPT];
+#pragma unroll
+        for (int u = 0; u < PPT; ++u) {
+          const int pos = base + tid * PPT + u;
+          np[u] = -1;
+          if (pos >= end) continue;
+          if (sdv[u]) np[u] = sl.start + cnt_a + rank_b++;
+          else np[u] = sl.start + (pos - sl.start - rank_b);   // side-a points before = offset - side-b before
+          if (np[u] < sl.start || np[u] >= sl.start + sl.count) {
+            record_error(a.ctrl, HDF_EDOMAIN);   // inconsistent counts: never write outside
+            np[u] = -1;
+          }
+        }
+#pragma unroll
+        for (int u0 = 0; u0 < PPT; u0 += UB) {
+          float x[UB][RMAX];
+          uint32_t pid[UB];
+#pragma unroll
+          for (int b = 0; b < UB; ++b) {
+            const int pos = base + tid * PPT + u0 + b;
+            const bool v = np[u0 + b] >= 0;
+            pid[b] = v ? __ldcg(a.perm + pos) : 0u;
+#pragma unroll
+            for (int d = 0; d < RMAX; ++d) x[b][d] = (v && d < rho) ? xat(a, d, pos) : 0.0f;
+          }
+#pragma unroll
+          for (int b = 0; b < UB; ++b) {
+            const int q = np[u0 + b];
+            if (q < 0) continue;
+            a.perm2[q] = pid[b];
+#pragma unroll
+            for (int d = 0; d < RMAX; ++d)
+              if (d < rho) a.X2[(size_t)d * N + q] = x[b][d];
+          }
+        }
+      }
+    }
+    if (!grid_barrier(a, gen, s, TR_SCATTER)) return;
+
+    // ---- children: segments, sums, SSE and farthest points
+    const int first = nnodes;
+    if (tid == 0) {
+      s.nseg = 2 * s.nslots;
+      for (int i = 0; i < s.nslots; ++i) {
+        const SlotRec& sl = s.slot[i];
+        const int ca = sl.count - sl.cnt_b_acc;
+        s.seg_start[2 * i] = sl.start;
+        s.seg_count[2 * i] = ca;
+        s.seg_start[2 * i + 1] = sl.start + ca;
+        s.seg_count[2 * i + 1] = sl.cnt_b_acc;
+        s.seg_on[2 * i] = sl.split;
+        s.seg_on[2 * i + 1] = sl.split;
+      }
+    }
+    __syncthreads();
+    // the centres of the accepted assignment are the children's means
+    for (int v = tid; v < s.nslots * rho; v += CL_THREADS) {
+      const int i = v / rho, d = v % rho;
+      const SlotRec& sl = s.slot[i];
+      if (!sl.split || bid != 0) continue;
+      const double tot = nsum[i * rho + d];
+      const double sb = acc_sum[i * rho + d];
+      a.node_sum[(size_t)(first + 2 * i) * rho + d] = tot - sb;
+      a.node_sum[(size_t)(first + 2 * i + 1) * rho + d] = sb;
+    }
+    __syncthreads();
+    build_chunks(s);
+    if (!dist_stats(true)) return;
+    if (bid == 0 && tid == 0) {
+      for (int i = 0; i < s.nslots; ++i) {
+        const SlotRec& sl = s.slot[i];
+        if (!sl.split) {
+          a.nodes[sl.node].sse = 0.0;   // not splittable: never chosen again
+          continue;
+        }
+        for (int w = 0; w < 2; ++w) {
+          NodeRec r;
+          r.start = s.seg_start[2 * i + w];
+          r.count = s.seg_count[2 * i + w];
+          r.child0 = -1;
+          r.far_idx = s.segarg[2 * i + w];
+          r.sse = s.segsse[2 * i + w];
+          a.nodes[first + 2 * i + w] = r;
+        }
+        a.nodes[sl.node].child0 = first + 2 * i;
+      }
+    }
+    nnodes += 2 * s.nslots;
+    if (!grid_barrier(a, gen, s, TR_CHILD)) return;
+  }
+
+  // ------------------------------------------------------------ outputs
+  // Leaves of the final replay are the clusters; s.leaf_cl holds the index.
+  if (tid == 0) {
+    s.nseg = s.nleaves;
+    for (int i = 0; i < s.nleaves; ++i) {
+      const int nd = s.leaf_node[i];
+      s.seg_start[i] = __ldcg(&a.nodes[nd].start);
+      s.seg_count[i] = __ldcg(&a.nodes[nd].count);
+      s.seg_on[i] = 1;
+    }
+  }
+  __syncthreads();
+  if (bid == 0) {
+    for (int v = tid; v < s.nleaves * rho; v += CL_THREADS) {
+      const int i = v / rho, d = v % rho;
+      const double m = __ldcg(a.node_sum + (size_t)s.leaf_node[i] * rho + d) / (double)s.seg_count[i];
+      a.mu64[s.leaf_cl[i] * rho + d] = m;
+      a.mu[s.leaf_cl[i] * rho + d] = (float)m;
+    }
+    if (tid == 0) {
+      double ek = 0.0;
+      for (int c = 0; c < s.nleaves; ++c)
+        for (int i = 0; i < s.nleaves; ++i)
+          if (s.leaf_cl[i] == c) ek += __ldcg(&a.nodes[s.leaf_node[i]].sse);
+      *a.ek = ek;
+      a.ctrl[CTRL_K_EFF] = s.nclusters;
+      a.ctrl[CTRL_LLOYD_MAX] = lloyd_max;
+      a.ctrl[CTRL_ROUNDS] = rounds;
+    }
+  }
+  // labels: one segment per cluster (MAXSEG >= HDF_MAX_K)
+  build_chunks(s);
+  for_blocks(a, s,
+      [&](int seg, int base, int end, int) {
+        uint32_t idx[PPT];
+#pragma unroll
+        for (int u = 0; u < PPT; ++u) {
+          const int pos = base + u * CL_THREADS + tid;
+          idx[u] = (pos < end) ? __ldcg(a.perm + pos) : 0xffffffffu;
+        }
+#pragma unroll
+        for (int u = 0; u < PPT; ++u)
+          if (idx[u] < (uint32_t)a.N) a.labels[idx[u]] = s.leaf_cl[seg];
+      },
+      [&](int) {});
+}
+
+
+// Host: cooperative launch of one instantiation.
+template <int RMAX>
+cudaError_t launch_cl(const ClArgs& a, int G, cudaStream_t st) {
+  const size_t smem = dyn_smem_bytes(a.rho);
+  cudaError_t e = cudaFuncSetAttribute(cluster_kernel<RMAX>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, occ = 0;
+  cudaGetDevice(&dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cluster_kernel<RMAX>, CL_THREADS,
+                                                    smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorCooperativeLaunchTooLarge;
+  void* args[] = {(void*)&a};
+  return cudaLaunchCooperativeKernel((const void*)cluster_kernel<RMAX>, dim3(G),
+                                     dim3(CL_THREADS), args, smem, st);
+}
+
+}  // namespace
+}  // namespace clus
+}  // namespace hdf

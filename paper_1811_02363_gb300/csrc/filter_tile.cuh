@@ -1,215 +1,241 @@
-// Fused convolution + combine of Algorithm 1 (loop "for3" and the final
-// division, Eq. (15)-(16)) for one output tile per CTA.
+// Fused convolution + combine of Algorithm 1 (loop "for3", the sums of
+// Eq. (15)-(16) before the division) for one output tile and one chunk of
+// P "planes" per CTA.  Plane 0 is the denominator plane (omega * b_k, summed
+// with weights c_k into sum_k c_k r_k); plane 1 + c is channel c of
+// u_k = b_k f (summed into sum_k c_k v_k).
 //
-// For each chunk of P "planes" (plane 0 is the denominator plane b_k, plane
-// 1 + c is channel c of u_k = b_k f) and each centre k:
-//   1. stage the halo tile of b_k (from the range-map planes) in shared memory;
-//   2. row pass: H = omega_1 (*) U on every halo row, U = b_k * f formed on the
-//      fly from the staged image tile (kept for all k of the chunk);
-//   3. column pass: V = omega_1 (*) H at the tile's pixels, and accumulate
-//      c_k(i) V(i) in registers (sum_k c_k v_k and sum_k c_k r_k of Eq. (15)-(16)).
+// Per centre k, with the halo tile of b_k double-buffered in shared memory by
+// cp.async (zero-filled outside the image = the zero extension of the sums):
+//   row pass:    H = omega_1 (*) (b_k f) on every halo row (b_k f formed on
+//                the fly from the image tile, staged once per CTA);
+//   column pass: V = omega_1 (*) H at the tile's pixels, acc += c_k(i) V(i).
 // The window W = [-S, S]^2 factorises, omega(j) = omega_1(j_1) omega_1(j_2),
-// so the two 1-D passes give exactly the 2-D sum over W (Sec. II-B); pixels
-// outside the image contribute nothing (zero extension).
+// so the two 1-D passes give exactly the 2-D sum over W (Sec. II-B).
 //
-// Template parameters: SB = compiled half-width (taps beyond the call's S are
-// zero weights), P = planes per chunk, TY = tile height.  The tile is 32
-// pixels wide; 256 threads; each thread owns YV consecutive rows of one
-// column of one plane across the whole k loop.
+// Template parameters: SB = compiled half-width (taps beyond the call's S
+// are zero weights), P = planes per CTA, TY = tile height.  Tile width 32,
+// 512 threads; each thread owns YV consecutive rows of one column of one
+// plane for the whole k loop.  Outputs: the numerator planes (unnormalised)
+// into g, and for the chunk holding plane 0 the denominator and max_k r_k
+// into per-pixel scratch, normalised afterwards by the divide kernel.
 #pragma once
 
 #include "hdf_internal.cuh"
 
 namespace hdf {
 
-constexpr float kGuardRel = 1e-6f;
-
 struct FilterArgs {
   const float* f;       // (n, H, W)
   const float* B;       // (K, H, W) range maps b_k
   const float* C;       // (K, H, W) coefficients c_k
-  float* g;             // (n, H, W)
-  int* ctrl;
-  int* fix_list;
+  float* g;             // (n, H, W) numerator sum_k c_k v_k (normalised later)
+  float* den;           // (H, W) sum_k c_k r_k
+  float* rmax;          // (H, W) max_k r_k
+  const int* ctrl;
   int H, W, n;
 };
+
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int bytes = valid ? 4 : 0;   // 0 bytes read: the word is zero-filled
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+constexpr int round_ld(int need) {  // smallest stride >= need with stride % 32 == 4
+  return ((need + 27) / 32) * 32 + 4;
+}
 
 template <int SB, int P, int TY>
 struct TileCfg {
   static constexpr int TX = 32;
-  static constexpr int NT = 256;
-  static constexpr int YV = TX * TY * P / NT;         // column-pass outputs per thread
-  static constexpr int XH = (P == 4) ? 16 : 8;         // row-pass outputs per task
+  static constexpr int NT = 512;
+  static constexpr int YV = TX * TY * P / NT;          // column-pass outputs per thread
+  static constexpr int XH = 16;                         // row-pass outputs per task
   static constexpr int NSEG = TX / XH;
-  static constexpr int HR = TY + 2 * SB;               // halo rows
-  static constexpr int HC = TX + 2 * SB;               // halo columns
-  static constexpr int LD = HC + 1;                    // odd stride: conflict-free row reads
-  static constexpr int LDH = TX + 1;
-  static constexpr int SF = P * HR * LD;               // floats
+  static constexpr int NIN = XH + 2 * SB;               // row-pass inputs per task
+  static constexpr int NIN4 = (NIN + 3) / 4;            // 128-bit loads per task
+  static constexpr int HR = TY + 2 * SB;                // halo rows
+  static constexpr int HC = TX + 2 * SB;                // halo columns
+  static constexpr int LD = round_ld((NSEG - 1) * XH + 4 * NIN4);
+  static constexpr int LDH = round_ld(TX);
+  static constexpr int SF = P * HR * LD;                // floats
   static constexpr int SBF = HR * LD;
   static constexpr int SH = P * HR * LDH;
-  static constexpr int SD = TY * TX;
-  static constexpr size_t SMEM = sizeof(float) * (size_t)(SF + SBF + SH + 2 * SD);
-  static_assert(TY % YV == 0, "tile height must be a multiple of the per-thread run");
+  static constexpr int SR = TY * TX;
+  static constexpr size_t SMEM = sizeof(float) * (size_t)(SF + 2 * SBF + SH + SR);
+  static_assert(TY % YV == 0 && YV >= 1, "tile height must be a multiple of the per-thread run");
   static_assert(TX * (TY / YV) * P == NT, "one column run per thread");
+  static_assert(LD >= HC, "row stride must hold the halo");
 };
 
 template <int SB, int P, int TY>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(512, 1)
 filter_tile_kernel(const FilterArgs a, const Taps taps) {
   using Cfg = TileCfg<SB, P, TY>;
   constexpr int TX = Cfg::TX, NT = Cfg::NT, YV = Cfg::YV, XH = Cfg::XH, NSEG = Cfg::NSEG;
   constexpr int HR = Cfg::HR, HC = Cfg::HC, LD = Cfg::LD, LDH = Cfg::LDH;
-  constexpr int NTAP = 2 * SB + 1;
-  extern __shared__ float sm[];
+  constexpr int NIN4 = Cfg::NIN4, NTAP = 2 * SB + 1;
+  extern __shared__ __align__(16) float sm[];
   float* sF = sm;                        // [P][HR][LD] image channels of the chunk
-  float* sB = sF + Cfg::SF;              // [HR][LD]    b_k
-  float* sH = sB + Cfg::SBF;             // [P][HR][LDH] row-pass results
-  float* sD = sH + Cfg::SH;              // [TY][TX] denominator sum_k c_k r_k
-  float* sR = sD + Cfg::SD;              // [TY][TX] max_k r_k (guard)
+  float* sB0 = sF + Cfg::SF;             // [2][HR][LD] b_k, double-buffered
+  float* sH = sB0 + 2 * Cfg::SBF;        // [P][HR][LDH] row-pass results
+  float* sR = sH + Cfg::SH;              // [TY][TX] max_k r_k (plane 0 only)
 
   const int tid = threadIdx.x;
   const int H = a.H, W = a.W, n = a.n;
   const size_t N = (size_t)H * W;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int chunk = blockIdx.z;
   const int K = a.ctrl[CTRL_K_EFF];
-  const int nchunks = (n + 1 + P - 1) / P;
 
   // column-pass ownership: plane qv, column xv, rows yv0 .. yv0 + YV - 1
   const int qv = tid / (TX * (TY / YV));
   const int xv = tid % TX;
   const int yv0 = ((tid / TX) % (TY / YV)) * YV;
   const int gx = x0 + xv;
+  const int qgv = chunk * P + qv;        // global plane of this thread's column run
 
-  for (int i = tid; i < Cfg::SD; i += NT) sR[i] = 0.0f;
-
-  for (int chunk = 0; chunk < nchunks; ++chunk) {
-    // ---- stage the image channels of this chunk (halo included, zero outside)
-    for (int idx = tid; idx < P * HR * HC; idx += NT) {
-      const int q = idx / (HR * HC);
-      const int r = (idx / HC) % HR;
-      const int c = idx % HC;
-      const int ch = chunk * P + q - 1;
+  // ---- stage the image channels of this chunk and b_0 (cp.async, zero outside)
+  for (int idx = tid; idx < P * HR * HC; idx += NT) {
+    const int q = idx / (HR * HC);
+    const int r = (idx / HC) % HR;
+    const int c = idx % HC;
+    const int ch = chunk * P + q - 1;
+    const int yy = y0 - SB + r, xx = x0 - SB + c;
+    const bool ok = ch >= 0 && ch < n && yy >= 0 && yy < H && xx >= 0 && xx < W;
+    cp_async4(sF + (q * HR + r) * LD + c, ok ? a.f + (size_t)ch * N + (size_t)yy * W + xx : a.f, ok);
+  }
+  auto stage_b = [&](int k, float* dst) {
+    const float* Bk = a.B + (size_t)k * N;
+    for (int idx = tid; idx < HR * HC; idx += NT) {
+      const int r = idx / HC, c = idx % HC;
       const int yy = y0 - SB + r, xx = x0 - SB + c;
-      float v = 0.0f;
-      if (ch >= 0 && ch < n && yy >= 0 && yy < H && xx >= 0 && xx < W)
-        v = __ldg(a.f + (size_t)ch * N + (size_t)yy * W + xx);
-      sF[(q * HR + r) * LD + c] = v;
+      const bool ok = yy >= 0 && yy < H && xx >= 0 && xx < W;
+      cp_async4(dst + r * LD + c, ok ? Bk + (size_t)yy * W + xx : Bk, ok);
     }
-    float acc[YV];
-#pragma unroll
-    for (int o = 0; o < YV; ++o) acc[o] = 0.0f;
-    const int qgv = chunk * P + qv;      // global plane of this thread's column run
+  };
+  stage_b(0, sB0);
+  cp_async_commit();
+  for (int i = tid; i < Cfg::SR; i += NT) sR[i] = 0.0f;
 
-    for (int k = 0; k < K; ++k) {
-      __syncthreads();
-      const float* Bk = a.B + (size_t)k * N;
-      for (int idx = tid; idx < HR * HC; idx += NT) {
-        const int r = idx / HC, c = idx % HC;
-        const int yy = y0 - SB + r, xx = x0 - SB + c;
-        float v = 0.0f;
-        if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = __ldg(Bk + (size_t)yy * W + xx);
-        sB[r * LD + c] = v;
-      }
-      __syncthreads();
-      // ---- row pass over every halo row: H = omega_1 (*) (b_k f)
-      for (int task = tid; task < P * HR * NSEG; task += NT) {
-        const int q = task / (HR * NSEG);
-        const int rem = task % (HR * NSEG);
-        const int r = rem / NSEG, seg = rem % NSEG;
-        const int qg = chunk * P + q;
-        if (qg > n) continue;
-        const float* pb = sB + r * LD + seg * XH;
-        const float* pf = sF + (q * HR + r) * LD + seg * XH;
-        float in[XH + 2 * SB];
-        if (qg == 0) {
+  float acc[YV], cnext[YV];
 #pragma unroll
-          for (int t = 0; t < XH + 2 * SB; ++t) in[t] = pb[t];
-        } else {
+  for (int o = 0; o < YV; ++o) {
+    acc[o] = 0.0f;
+    const int gy = y0 + yv0 + o;
+    cnext[o] = (gy < H && gx < W) ? __ldg(a.C + (size_t)gy * W + gx) : 0.0f;
+  }
+
+  for (int k = 0; k < K; ++k) {
+    float* sB = sB0 + (k & 1) * Cfg::SBF;
+    if (k + 1 < K) stage_b(k + 1, sB0 + ((k + 1) & 1) * Cfg::SBF);
+    cp_async_commit();
+    cp_async_wait<1>();                  // everything but b_{k+1} has landed
+    __syncthreads();
+    float ccur[YV];
 #pragma unroll
-          for (int t = 0; t < XH + 2 * SB; ++t) in[t] = pb[t] * pf[t];
-        }
-        float* ph = sH + (q * HR + r) * LDH + seg * XH;
-#pragma unroll
-        for (int o = 0; o < XH; ++o) {
-          float h = 0.0f;
-#pragma unroll
-          for (int t = 0; t < NTAP; ++t) h = fmaf(taps.w[t], in[o + t], h);
-          ph[o] = h;
-        }
-      }
-      __syncthreads();
-      // ---- column pass at the tile's pixels, accumulate c_k V
-      if (qgv <= n) {
-        float in[YV + 2 * SB];
-        const float* ph = sH + (qv * HR + yv0) * LDH + xv;
-#pragma unroll
-        for (int t = 0; t < YV + 2 * SB; ++t) in[t] = ph[t * LDH];
-        const float* Ck = a.C + (size_t)k * N;
-#pragma unroll
-        for (int o = 0; o < YV; ++o) {
-          float v = 0.0f;
-#pragma unroll
-          for (int t = 0; t < NTAP; ++t) v = fmaf(taps.w[t], in[o + t], v);
-          const int gy = y0 + yv0 + o;
-          if (gy < H && gx < W) {
-            acc[o] = fmaf(__ldg(Ck + (size_t)gy * W + gx), v, acc[o]);
-            if (qgv == 0) {
-              float* pr = sR + (yv0 + o) * TX + xv;
-              *pr = fmaxf(*pr, v);
-            }
-          }
-        }
-      }
+    for (int o = 0; o < YV; ++o) {
+      ccur[o] = cnext[o];
+      const int gy = y0 + yv0 + o;
+      cnext[o] = (k + 1 < K && gy < H && gx < W)
+                     ? __ldg(a.C + (size_t)(k + 1) * N + (size_t)gy * W + gx) : 0.0f;
     }
-    // ---- end of the k loop for this chunk
-    if (chunk == 0 && qgv == 0) {
+    // ---- row pass over every halo row: H = omega_1 (*) (b_k f)
+    for (int task = tid; task < P * HR * NSEG; task += NT) {
+      const int q = task / (HR * NSEG);
+      const int rem = task % (HR * NSEG);
+      const int r = rem / NSEG, seg = rem % NSEG;
+      const int qg = chunk * P + q;
+      if (qg > n) continue;
+      const float4* pb = reinterpret_cast<const float4*>(sB + r * LD + seg * XH);
+      const float4* pf = reinterpret_cast<const float4*>(sF + (q * HR + r) * LD + seg * XH);
+      float in[4 * NIN4];
 #pragma unroll
-      for (int o = 0; o < YV; ++o) {
-        const int gy = y0 + yv0 + o;
-        float D = acc[o];
-        if (gy < H && gx < W) {
-          const float rmax = sR[(yv0 + o) * TX + xv];
-          if (!(D > kGuardRel * rmax)) {       // guard: take the indicator value later
-            const int pos = atomicAdd(a.ctrl + CTRL_FALLBACK, 1);
-            if (pos < (int)N) a.fix_list[pos] = gy * W + gx;
-            D = 1.0f;
-          }
+      for (int t = 0; t < NIN4; ++t) {
+        const float4 b = pb[t];
+        if (qg == 0) {
+          in[4 * t] = b.x; in[4 * t + 1] = b.y; in[4 * t + 2] = b.z; in[4 * t + 3] = b.w;
+        } else {
+          const float4 v = pf[t];
+          in[4 * t] = b.x * v.x; in[4 * t + 1] = b.y * v.y;
+          in[4 * t + 2] = b.z * v.z; in[4 * t + 3] = b.w * v.w;
         }
-        sD[(yv0 + o) * TX + xv] = D;
       }
+      float h[XH];
+#pragma unroll
+      for (int o = 0; o < XH; ++o) h[o] = 0.0f;
+#pragma unroll
+      for (int t = 0; t < NTAP; ++t) {
+#pragma unroll
+        for (int o = 0; o < XH; ++o) h[o] = fmaf(taps.w[t], in[o + t], h[o]);
+      }
+      float4* ph = reinterpret_cast<float4*>(sH + (q * HR + r) * LDH + seg * XH);
+#pragma unroll
+      for (int o = 0; o < XH / 4; ++o) ph[o] = make_float4(h[4 * o], h[4 * o + 1], h[4 * o + 2], h[4 * o + 3]);
     }
     __syncthreads();
-    if (qgv >= 1 && qgv <= n) {
-      float* gc = a.g + (size_t)(qgv - 1) * N;
+    // ---- column pass at the tile's pixels, accumulate c_k V
+    if (qgv <= n) {
+      float in[YV + 2 * SB];
+      const float* ph = sH + (qv * HR + yv0) * LDH + xv;
 #pragma unroll
-      for (int o = 0; o < YV; ++o) {
-        const int gy = y0 + yv0 + o;
-        if (gy < H && gx < W) gc[(size_t)gy * W + gx] = acc[o] / sD[(yv0 + o) * TX + xv];
+      for (int t = 0; t < YV + 2 * SB; ++t) in[t] = ph[t * LDH];
+      float v[YV];
+#pragma unroll
+      for (int o = 0; o < YV; ++o) v[o] = 0.0f;
+#pragma unroll
+      for (int t = 0; t < NTAP; ++t) {
+#pragma unroll
+        for (int o = 0; o < YV; ++o) v[o] = fmaf(taps.w[t], in[o + t], v[o]);
+      }
+#pragma unroll
+      for (int o = 0; o < YV; ++o) acc[o] = fmaf(ccur[o], v[o], acc[o]);
+      if (qgv == 0) {
+#pragma unroll
+        for (int o = 0; o < YV; ++o) {
+          float* pr = sR + (yv0 + o) * TX + xv;
+          *pr = fmaxf(*pr, v[o]);
+        }
+      }
+    }
+  }
+  // ---- write the sums of this chunk's planes
+  if (qgv <= n) {
+#pragma unroll
+    for (int o = 0; o < YV; ++o) {
+      const int gy = y0 + yv0 + o;
+      if (gy < H && gx < W) {
+        const size_t pix = (size_t)gy * W + gx;
+        if (qgv == 0) {
+          a.den[pix] = acc[o];
+          a.rmax[pix] = sR[(yv0 + o) * TX + xv];
+        } else {
+          a.g[(size_t)(qgv - 1) * N + pix] = acc[o];
+        }
       }
     }
   }
 }
 
-// Launch one instantiation; returns cudaErrorInvalidValue if it cannot hold
-// the call's window.
 template <int SB, int P, int TY>
 cudaError_t launch_filter_tile(const FilterArgs& a, const Taps& taps, cudaStream_t st) {
   using Cfg = TileCfg<SB, P, TY>;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(filter_tile_kernel<SB, P, TY>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Cfg::SMEM);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
-  dim3 grid((a.W + Cfg::TX - 1) / Cfg::TX, (a.H + TY - 1) / TY);
+  cudaError_t e = cudaFuncSetAttribute(filter_tile_kernel<SB, P, TY>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)Cfg::SMEM);
+  if (e != cudaSuccess) return e;
+  const int nchunks = (a.n + 1 + P - 1) / P;
+  dim3 grid((a.W + Cfg::TX - 1) / Cfg::TX, (a.H + TY - 1) / TY, nchunks);
   filter_tile_kernel<SB, P, TY><<<grid, Cfg::NT, Cfg::SMEM, st>>>(a, taps);
   return cudaGetLastError();
 }
 
-// Dispatch entry points, one per translation unit (compiled in parallel).
+// Dispatch entry point over the compiled (SB, P, TY) instantiations.
 cudaError_t launch_filter_sb(int SB, int P, const FilterArgs& a, const Taps& taps,
                              cudaStream_t st);
 

@@ -98,6 +98,8 @@ hdf_status hdf_create(hdf_handle** out, const hdf_desc* desc) {
   ok &= dalloc(&h->B, K * N) == cudaSuccess;
   ok &= dalloc(&h->C, K * N) == cudaSuccess;
   ok &= dalloc(&h->s, N) == cudaSuccess;
+  ok &= dalloc(&h->den, N) == cudaSuccess;
+  ok &= dalloc(&h->rmax, N) == cudaSuccess;
   ok &= dalloc(&h->fix_list, N) == cudaSuccess;
   ok &= dalloc(&h->grad_scratch, 1 << 16) == cudaSuccess;
   ok &= dalloc(&h->labels, N) == cudaSuccess;
@@ -131,6 +133,8 @@ void hdf_destroy(hdf_handle* h) {
   cudaFree(h->B);
   cudaFree(h->C);
   cudaFree(h->s);
+  cudaFree(h->den);
+  cudaFree(h->rmax);
   cudaFree(h->fix_list);
   cudaFree(h->grad_scratch);
   cudaFree(h->labels);
@@ -220,6 +224,12 @@ hdf_status hdf_bruteforce(const hdf_desc* desc, const float* d_f, const void* d_
   hdf_status s = check_desc(&d);
   if (s != HDF_OK) return s;
   HDF_CUDA(hdf::launch_bruteforce(d, d_f, d_p, d_g, (cudaStream_t)stream), "bruteforce");
+  return HDF_OK;
+}
+
+hdf_status hdf_get_trace(hdf_handle* h, int64_t* h_events, int cap, int* count, void* stream) {
+  if (!h || !h_events || !count || cap < 0) return HDF_EINVAL;
+  HDF_CUDA(hdf::cluster_trace(h, (long long*)h_events, cap, count, (cudaStream_t)stream), "trace");
   return HDF_OK;
 }
 

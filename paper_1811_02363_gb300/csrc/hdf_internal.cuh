@@ -61,6 +61,8 @@ struct hdf_handle {
   float* B;           // K x N range maps b_k(i)
   float* C;           // K x N coefficients c_k(i)
   uint8_t* s;         // N nearest centre (Voronoi cell) per pixel
+  float* den;         // N denominator sum_k c_k r_k of the last apply
+  float* rmax;        // N max_k r_k of the last apply (guard)
   int* fix_list;      // N pixels that take the denominator guard
   double* grad_scratch;  // backward partial sums
   // clustering workspace (allocated in hdf_create, sized by N)
@@ -80,6 +82,7 @@ cudaError_t launch_bruteforce(const hdf_desc& d, const float* f, const void* p, 
                               cudaStream_t st);
 cudaError_t launch_cluster(hdf_handle* h, const void* p, cudaStream_t st);
 size_t cluster_workspace_bytes(int N, int rho, int K);
+cudaError_t cluster_trace(hdf_handle* h, long long* host, int cap, int* count, cudaStream_t st);
 cudaError_t launch_backward(hdf_handle* h, const float* f, const void* p, const float* G,
                             float* grad_f, double* grad_ls, cudaStream_t st);
 

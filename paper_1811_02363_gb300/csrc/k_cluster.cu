@@ -1,10 +1,136 @@
-// Bisecting K-means (placeholder until the clustering kernel lands).
-#include "hdf_internal.cuh"
+// Host side of the clustering stage (Algorithm 1 "cluster", Sec. II-C):
+// workspace layout, grid size and dispatch to the per-dimension
+// instantiations of the cooperative kernel (cluster_kernel.cuh), which are
+// compiled in separate translation units.
+#include "cluster_kernel.cuh"
 
 namespace hdf {
 
-size_t cluster_workspace_bytes(int N, int rho, int K) { return 256; }
+cudaError_t launch_cluster_r4(const clus::ClArgs&, int, cudaStream_t);
+cudaError_t launch_cluster_r8(const clus::ClArgs&, int, cudaStream_t);
+cudaError_t launch_cluster_r16(const clus::ClArgs&, int, cudaStream_t);
+cudaError_t launch_cluster_r32(const clus::ClArgs&, int, cudaStream_t);
+cudaError_t launch_cluster_r64(const clus::ClArgs&, int, cudaStream_t);
 
-cudaError_t launch_cluster(hdf_handle*, const void*, cudaStream_t) { return cudaErrorNotSupported; }
+namespace {
+using namespace clus;
+
+// ---------------------------------------------------------------- host side
+
+struct Layout {
+  size_t perm, perm2, X, X2, side, marg, d32, nodes, node_sum, pf, pi, pd, pdd, px, chunk_cnt, trace, fin,
+      total;
+};
+
+int grid_blocks(int dev) {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;   // one block per SM (co-residency of a cooperative launch)
+}
+
+Layout layout(int N, int rho, int G) {
+  Layout L;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o += (bytes + 255) & ~(size_t)255;
+    return at;
+  };
+  const size_t maxchunks = (size_t)N / CH + MAXSEG + 2;
+  L.perm = take(sizeof(uint32_t) * (size_t)N);
+  L.perm2 = take(sizeof(uint32_t) * (size_t)N);
+  L.X = take(sizeof(float) * (size_t)N * rho);
+  L.X2 = take(sizeof(float) * (size_t)N * rho);
+  L.side = take(2 * (size_t)N);
+  L.marg = take(sizeof(float) * (size_t)N);
+  L.d32 = take(sizeof(float) * (size_t)N);
+  L.nodes = take(sizeof(NodeRec) * MAXNODES);
+  L.node_sum = take(sizeof(double) * MAXNODES * (size_t)rho);
+  L.pf = take(sizeof(float) * 2 * (size_t)G * MAXSEG * (rho + 1));
+  L.pi = take(sizeof(int) * (size_t)G * MAXSEG * 2);
+  L.pd = take(sizeof(float) * (size_t)G * MAXSEG);
+  L.pdd = take(sizeof(double) * (size_t)G * MAXSEG);
+  L.px = take(sizeof(int) * (size_t)G * MAXSEG);
+  L.chunk_cnt = take(sizeof(int) * maxchunks);
+  L.trace = take(sizeof(long long) * (1 + 2 * TRACE_CAP));
+  L.fin = take(sizeof(double) * MAXACT * (size_t)(rho + 2));
+  L.total = o;
+  return L;
+}
+
+}  // namespace
+
+size_t cluster_workspace_bytes(int N, int rho, int K) {
+  (void)K;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return layout(N, rho, grid_blocks(dev)).total;
+}
+
+cudaError_t launch_cluster(hdf_handle* h, const void* p, cudaStream_t st) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int G = grid_blocks(dev);
+  const Layout L = layout(h->N, h->d.rho, G);
+  if (L.total > h->cl_ws_bytes) return cudaErrorInvalidValue;
+  unsigned char* w = (unsigned char*)h->cl_ws;
+  ClArgs a;
+  a.p = p;
+  a.N = h->N;
+  a.rho = h->d.rho;
+  a.K = h->d.K;
+  a.G = G;
+  a.ctrl = h->ctrl;
+  a.mu = h->mu;
+  a.mu64 = h->mu64;
+  a.labels = h->labels;
+  a.ek = h->ek;
+  a.perm = (uint32_t*)(w + L.perm);
+  a.perm2 = (uint32_t*)(w + L.perm2);
+  a.X = (float*)(w + L.X);
+  a.X2 = (float*)(w + L.X2);
+  a.side = w + L.side;
+  a.marg = (float*)(w + L.marg);
+  a.d32 = (float*)(w + L.d32);
+  a.nodes = (NodeRec*)(w + L.nodes);
+  a.node_sum = (double*)(w + L.node_sum);
+  a.pf = (float*)(w + L.pf);
+  a.pi = (int*)(w + L.pi);
+  a.pd = (float*)(w + L.pd);
+  a.pdd = (double*)(w + L.pdd);
+  a.px = (int*)(w + L.px);
+  a.chunk_cnt = (int*)(w + L.chunk_cnt);
+  a.trace = (long long*)(w + L.trace);
+  a.fin = (double*)(w + L.fin);
+  // barrier words start from zero for every launch
+  cudaError_t e = cudaMemsetAsync(h->ctrl + CTRL_BARRIER, 0, 2 * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(a.trace, 0, sizeof(long long), st);
+  if (e != cudaSuccess) return e;
+  a.p_bf16 = h->d.guide_dtype == HDF_GUIDE_BF16 ? 1 : 0;
+  if (a.rho <= 4) return launch_cluster_r4(a, G, st);
+  if (a.rho <= 8) return launch_cluster_r8(a, G, st);
+  if (a.rho <= 16) return launch_cluster_r16(a, G, st);
+  if (a.rho <= 32) return launch_cluster_r32(a, G, st);
+  return launch_cluster_r64(a, G, st);
+}
+
+cudaError_t cluster_trace(hdf_handle* h, long long* host, int cap, int* count, cudaStream_t st) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const Layout L = layout(h->N, h->d.rho, grid_blocks(dev));
+  const long long* t = (const long long*)((unsigned char*)h->cl_ws + L.trace);
+  long long n = 0;
+  cudaError_t e = cudaMemcpyAsync(&n, t, sizeof(n), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  if (n > cap) n = cap;
+  if (n > 0) {
+    e = cudaMemcpyAsync(host, t + 1, sizeof(long long) * 2 * (size_t)n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  *count = (int)n;
+  return e;
+}
 
 }  // namespace hdf

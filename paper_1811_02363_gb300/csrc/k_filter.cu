@@ -9,6 +9,8 @@
 namespace hdf {
 namespace {
 
+constexpr float kGuardRel = 1e-6f;   // guard: sum_k c_k r_k <= 1e-6 max_k r_k
+
 constexpr int RM_THREADS = 256;
 
 // b_k(i) = phi(mu_k - p(i)) (Eq. (12)), computed from direct differences in
@@ -122,6 +124,23 @@ __global__ void fixup_kernel(const float* __restrict__ f, const float* __restric
   }
 }
 
+// Eq. (15)-(16): g_hat = (sum_k c_k v_k) / (sum_k c_k r_k) per pixel, with the
+// denominator guard; guarded pixels are listed for the indicator fix-up.
+__global__ void divide_kernel(float* __restrict__ g, const float* __restrict__ den,
+                              const float* __restrict__ rmax, int* __restrict__ ctrl,
+                              int* __restrict__ fix_list, int N, int n) {
+  for (int pix = blockIdx.x * blockDim.x + threadIdx.x; pix < N; pix += gridDim.x * blockDim.x) {
+    const float D = den[pix];
+    if (!(D > kGuardRel * rmax[pix])) {
+      const int pos = atomicAdd(ctrl + CTRL_FALLBACK, 1);
+      if (pos < N) fix_list[pos] = pix;
+      continue;
+    }
+    const float inv = 1.0f / D;
+    for (int c = 0; c < n; ++c) g[(size_t)c * N + pix] *= inv;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_rangemap(hdf_handle* h, const void* p, cudaStream_t st) {
@@ -154,12 +173,13 @@ cudaError_t launch_filter(hdf_handle* h, const float* f, float* g, cudaStream_t 
   for (int j = -d.S; j <= d.S; ++j) taps.w[SB + j] = exact.w[d.S + j];
   cudaError_t e = cudaMemsetAsync(h->ctrl + CTRL_FALLBACK, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  FilterArgs a{f, h->B, h->C, g, h->ctrl, h->fix_list, d.H, d.W, d.n};
+  FilterArgs a{f, h->B, h->C, g, h->den, h->rmax, h->ctrl, d.H, d.W, d.n};
   e = launch_filter_sb(SB, P, a, taps, st);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  divide_kernel<<<sms * 4, 256, 0, st>>>(g, h->den, h->rmax, h->ctrl, h->fix_list, h->N, d.n);
   fixup_kernel<<<sms, 256, 0, st>>>(f, h->B, h->s, h->fix_list, h->ctrl, d.H, d.W, d.n, d.S,
                                     exact, g);
   return cudaGetLastError();

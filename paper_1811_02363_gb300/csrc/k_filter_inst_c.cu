@@ -10,7 +10,7 @@ cudaError_t launch_filter_group_c(int SB, int P, const FilterArgs& a, const Taps
   switch (SB) {
     case 18: return launch_filter_tile<18, 2, 64>(a, t, st);
     case 24: return launch_filter_tile<24, 2, 64>(a, t, st);
-    case 32: return launch_filter_tile<32, 2, 64>(a, t, st);
+    case 32: return launch_filter_tile<32, 2, 32>(a, t, st);
   }
   return cudaErrorNotSupported;
 }

@@ -1,0 +1,69 @@
+"""hdf_apply_static: the fast-filter apply for callers that cannot allocate
+device memory (graph capture, frameworks that own all device memory, latency
+-critical paths).  Its output must match the allocating path (hdf_create +
+hdf_set_centers + hdf_apply) on the same centres, call after call, although
+every call reuses the same static scratch array.  Kept in a file collected
+last so that a stop at its failure comes after every other test."""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import hdfilter_oracle as O
+from paper_1811_02363_gb300 import synthetic
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4   # max-abs, the float32 tolerance of the other parity tests
+
+
+@pytest.fixture(scope="module")
+def mods():
+    from paper_1811_02363_gb300 import build
+    build.build()
+    from paper_1811_02363_gb300 import _lib, api
+    return _lib, api
+
+
+def _static_apply(L, api, f, mu, sigma_s, sigma_r, out):
+    n, H, W = f.shape
+    d = api.make_desc(H, W, n, n, mu.shape[0], sigma_s, sigma_r)
+    code = L.lib().hdf_apply_static(C.byref(d), C.c_void_p(mu.data_ptr()), mu.shape[0],
+                                    C.c_void_p(f.data_ptr()), C.c_void_p(f.data_ptr()),
+                                    C.c_void_p(out.data_ptr()),
+                                    C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    return code
+
+
+@pytest.mark.parametrize("case", [("rgb", 96, 80, 8, 3.0, 0.2), ("hyper16", 70, 64, 16, 2.0, 0.25)])
+def test_static_apply_matches_allocating_apply_twice(mods, case):
+    L, api = mods
+    name, H, W, K, ss, sr = case
+    results = []
+    for call, seed in enumerate((61, 62)):   # two calls in a row on different inputs
+        if name == "rgb":
+            f_np = synthetic.color_rectangles(H, W, seed=seed)
+        else:
+            f_np = synthetic.hyperspectral_mixture(H, W, bands=16, seed=seed)
+        n = f_np.shape[0]
+        mu_np = O.bisecting_kmeans(f_np.reshape(n, -1).T.astype(np.float64), K)[0].astype(np.float32)
+        f = torch.from_numpy(f_np).cuda()
+        ref = api.HDFilter(H, W, n, n, mu_np.shape[0], ss, sr)
+        ref.set_centers(mu_np)
+        g_ref = ref.apply(f)
+        mu = torch.from_numpy(mu_np).cuda()
+        g = torch.full_like(f, float("nan"))
+        assert _static_apply(L, api, f, mu, ss, sr, g) == L.HDF_OK
+        torch.cuda.synchronize()
+        err = float((g - g_ref).abs().max())
+        assert err <= TOL, (call, err)
+        results.append(err)
+    assert len(results) == 2
+
+
+def test_static_apply_rejects_oversized_requests(mods):
+    L, api = mods
+    f = torch.zeros((31, 512, 512), device="cuda")
+    mu = torch.zeros((32, 31), device="cuda")
+    g = torch.empty_like(f)
+    assert _static_apply(L, api, f, mu, 5.0, 0.3, g) == L.HDF_EUNSUPPORTED

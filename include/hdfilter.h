@@ -172,6 +172,18 @@ hdf_status hdf_backward(hdf_handle* h, const float* d_f, const void* d_p,
 hdf_status hdf_apply_static(const hdf_desc* desc, const float* d_mu, int K, const float* d_f,
                             const void* d_p, float* d_g, void* stream);
 
+/* Guide for nonlocal means (Sec. I-A; PCA-NLM, Sec. III-C): the patch x patch
+ * neighbourhood of every channel around each pixel (borders mirrored without
+ * repeating the edge pixel) is reduced by PCA -- mean patch subtracted,
+ * covariance over all pixels, projection on the desc.rho eigenvectors of
+ * largest eigenvalue (FP64 eigendecomposition on the device).
+ *   d_f: image (desc.n, H, W) float32;  d_p: output guide (desc.rho, H, W)
+ *   float32, usable as the guide of hdf_cluster / hdf_apply.
+ * Eigenvector signs are arbitrary (the filter only uses distances).  Limits:
+ * odd patch, desc.n * patch^2 <= 96, desc.n <= 4, H, W > patch/2; otherwise
+ * HDF_EUNSUPPORTED / HDF_EINVAL.  Asynchronous, allocates nothing. */
+hdf_status hdf_nlm_guide(hdf_handle* h, const float* d_f, int patch, float* d_p, void* stream);
+
 /* Brute-force filter, Eq. (1)-(2), by direct summation over the window.
  * Same layouts as hdf_apply.  Asynchronous, allocates nothing. */
 hdf_status hdf_bruteforce(const hdf_desc* desc, const float* d_f, const void* d_p,

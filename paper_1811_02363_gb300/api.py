@@ -144,6 +144,22 @@ class HDFilter:
                                      _stream()), "hdf_backward")
         return gf, gs[0], gs[1]
 
+    def _check_sigmas(self, log_sigma_s: float, log_sigma_r: float) -> None:
+        for name, lv, ref in (("sigma_s", log_sigma_s, self.desc.sigma_s),
+                              ("sigma_r", log_sigma_r, self.desc.sigma_r)):
+            if abs(math.exp(lv) - ref) > 1e-6 * ref:   # float32 log-sigma tensors
+                raise ValueError(f"{name}={math.exp(lv)} differs from the filter's {ref}; "
+                                 "create a filter for the new value")
+
+    def nlm_guide(self, f: torch.Tensor, patch: int = 7, out: torch.Tensor | None = None) -> torch.Tensor:
+        """PCA-reduced patch guide (desc.rho features) of the image f (n, H, W)."""
+        self._check_f(f)
+        p = out if out is not None else torch.empty((self.desc.rho, self.desc.H, self.desc.W),
+                                                    dtype=torch.float32, device=f.device)
+        L.check(L.lib().hdf_nlm_guide(self._h, _ptr(f), int(patch), _ptr(p), _stream()),
+                "hdf_nlm_guide")
+        return p
+
     def trace(self, cap: int = 2048) -> np.ndarray:
         """(phase, ns) events of the last clustering (see hdf_get_trace)."""
         buf = np.zeros(2 * cap, dtype=np.int64)
@@ -178,3 +194,33 @@ def bruteforce(f: torch.Tensor, p: torch.Tensor | None, sigma_s: float, sigma_r:
     L.check(L.lib().hdf_bruteforce(C.byref(d), _ptr(f), _ptr(p), _ptr(g), _stream()),
             "hdf_bruteforce")
     return g
+
+
+class _FastFilterFn(torch.autograd.Function):
+    """g = fast filter of f (guide = f or a fixed separate guide); gradients
+    for f, log sigma_s and log sigma_r from hdf_backward (centres and S fixed)."""
+
+    @staticmethod
+    def forward(ctx, f, log_sigma_s, log_sigma_r, flt, guide):
+        flt._check_sigmas(float(log_sigma_s), float(log_sigma_r))
+        p = f if guide is None else guide
+        g = flt.apply(f.contiguous(), p)
+        ctx.flt = flt
+        ctx.guide = guide
+        ctx.save_for_backward(f)
+        return g
+
+    @staticmethod
+    def backward(ctx, grad_g):
+        (f,) = ctx.saved_tensors
+        p = f if ctx.guide is None else ctx.guide
+        gf, gls, glr = ctx.flt.backward(f.contiguous(), p, grad_g.contiguous())
+        return gf, gls.to(torch.float32), glr.to(torch.float32), None, None
+
+
+def fast_filter(f: torch.Tensor, log_sigma_s: torch.Tensor, log_sigma_r: torch.Tensor,
+                flt: HDFilter, guide: torch.Tensor | None = None) -> torch.Tensor:
+    """Differentiable fast filter (Algorithm 1) with the centres installed in
+    ``flt``.  ``exp(log_sigma_*)`` must equal the filter's sigmas (the handle
+    fixes them and S); gradients flow to f, log_sigma_s and log_sigma_r."""
+    return _FastFilterFn.apply(f, log_sigma_s, log_sigma_r, flt, guide)

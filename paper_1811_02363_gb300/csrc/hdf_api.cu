@@ -103,6 +103,17 @@ hdf_status hdf_create(hdf_handle** out, const hdf_desc* desc) {
   ok &= dalloc(&h->fix_list, N) == cudaSuccess;
   ok &= dalloc(&h->grad_scratch, 1 << 16) == cudaSuccess;
   ok &= dalloc(&h->labels, N) == cudaSuccess;
+  ok &= dalloc(&h->bw_g, (size_t)d.n * N) == cudaSuccess;
+  ok &= dalloc(&h->bw_lam, (size_t)(d.n + 1) * N) == cudaSuccess;
+  ok &= dalloc(&h->bw_gam, K * N) == cudaSuccess;
+  ok &= dalloc(&h->bw_bet, K * N) == cudaSuccess;
+  ok &= dalloc(&h->bw_flag, N) == cudaSuccess;
+  {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    h->nlm_ws_bytes = hdf::nlm_workspace_bytes(sms > 0 ? sms : 1);
+  }
+  ok &= cudaMalloc(&h->nlm_ws, h->nlm_ws_bytes) == cudaSuccess;
   h->cl_ws_bytes = hdf::cluster_workspace_bytes(h->N, d.rho, d.K);
   ok &= cudaMalloc(&h->cl_ws, h->cl_ws_bytes) == cudaSuccess;
   if (!ok) {
@@ -138,7 +149,13 @@ void hdf_destroy(hdf_handle* h) {
   cudaFree(h->fix_list);
   cudaFree(h->grad_scratch);
   cudaFree(h->labels);
+  cudaFree(h->bw_g);
+  cudaFree(h->bw_lam);
+  cudaFree(h->bw_gam);
+  cudaFree(h->bw_bet);
+  cudaFree(h->bw_flag);
   cudaFree(h->cl_ws);
+  cudaFree(h->nlm_ws);
   delete h;
 }
 
@@ -214,6 +231,17 @@ hdf_status hdf_backward(hdf_handle* h, const float* d_f, const void* d_p, const 
   cudaStream_t st = (cudaStream_t)stream;
   HDF_CUDA(hdf::launch_backward(h, d_f, d_p, d_grad_g, d_grad_f, d_grad_log_sigma, st),
            "backward");
+  return HDF_OK;
+}
+
+hdf_status hdf_nlm_guide(hdf_handle* h, const float* d_f, int patch, float* d_p, void* stream) {
+  if (!h || !d_f || !d_p || patch < 1 || (patch & 1) == 0) return HDF_EINVAL;
+  const hdf_desc& d = h->d;
+  if (d.n * patch * patch > 96 || d.n > 4 || d.rho > d.n * patch * patch) return HDF_EUNSUPPORTED;
+  if (d.H < patch / 2 + 1 || d.W < patch / 2 + 1) return HDF_EINVAL;
+  HDF_CUDA(hdf::launch_nlm_guide(d_f, d.n, d.H, d.W, patch, d.rho, d_p, h->nlm_ws, h->nlm_ws_bytes,
+                                 h->ctrl, (cudaStream_t)stream),
+           "nlm_guide");
   return HDF_OK;
 }
 

@@ -17,6 +17,7 @@ enum CtrlSlot {
   CTRL_FALLBACK = 2,     // pixels that took the denominator guard in the last apply
   CTRL_LLOYD_MAX = 3,    // largest 2-means iteration count of the last clustering
   CTRL_ROUNDS = 4,       // split rounds of the last clustering
+  CTRL_RANKDEF = 5,      // 1 if the last fit dropped eigenvalues of A (truncated pseudo-inverse)
   CTRL_BARRIER = 8,      // grid barrier: arrival counter
   CTRL_BARRIER_GEN = 9,  // grid barrier: generation
   CTRL_WORDS = 16
@@ -69,6 +70,14 @@ struct hdf_handle {
   void* cl_ws;
   size_t cl_ws_bytes;
   int32_t* labels;    // N labels of the last clustering
+  // backward scratch
+  float* bw_g;        // n x N recomputed g_hat
+  float* bw_lam;      // (n+1) x N lambda planes
+  float* bw_gam;      // K x N gamma_k
+  float* bw_bet;      // K x N direct part of dL/db_k
+  uint8_t* bw_flag;   // N pixels that took the denominator guard
+  void* nlm_ws;       // NLM guide workspace
+  size_t nlm_ws_bytes;
 };
 
 namespace hdf {
@@ -82,6 +91,9 @@ cudaError_t launch_bruteforce(const hdf_desc& d, const float* f, const void* p, 
                               cudaStream_t st);
 cudaError_t launch_cluster(hdf_handle* h, const void* p, cudaStream_t st);
 size_t cluster_workspace_bytes(int N, int rho, int K);
+size_t nlm_workspace_bytes(int G);
+cudaError_t launch_nlm_guide(const float* f, int n, int H, int W, int m, int rho, float* p,
+                             void* ws, size_t ws_bytes, int* ctrl, cudaStream_t st);
 cudaError_t cluster_trace(hdf_handle* h, long long* host, int cap, int* count, cudaStream_t st);
 cudaError_t launch_backward(hdf_handle* h, const float* f, const void* p, const float* G,
                             float* grad_f, double* grad_ls, cudaStream_t st);

@@ -74,6 +74,7 @@ fit_kernel(const float* __restrict__ mu, int rho, int* ctrl, double inv2sr2,
     __syncthreads();
   }
   bool full_rank = false;
+  if (tid == 0) ctrl[CTRL_RANKDEF] = 0;
   if (s_flag) {
     // Column c of L^{-1} by forward substitution (one thread per column),
     // stored transposed: X[c*K + i] = (L^{-1})_{i c}.
@@ -184,6 +185,11 @@ fit_kernel(const float* __restrict__ mu, int rho, int* ctrl, double inv2sr2,
     double lmax = 0.0;
     for (int m = 0; m < K; ++m) lmax = fmax(lmax, fabs(X[m * K + m]));
     const double tol = matlab_tol(lmax, K);
+    if (tid == 0) {
+      int dropped = 0;
+      for (int m = 0; m < K; ++m) dropped += !(fabs(X[m * K + m]) > tol);
+      ctrl[CTRL_RANKDEF] = dropped > 0;
+    }
     for (int idx = tid; idx < K * K; idx += nt) {
       const int k = idx / K, l = idx % K;
       double s = 0.0;

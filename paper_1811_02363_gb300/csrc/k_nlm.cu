@@ -1,0 +1,325 @@
+// Guide for nonlocal means: every pixel's patch (patch x patch pixels of each
+// channel around it; Sec. I-A), reduced by PCA to rho features (PCA-NLM,
+// Sec. III-C): subtract the mean patch, take the eigenvectors of the patch
+// covariance with the rho largest eigenvalues, project.  Borders are mirrored
+// without repeating the edge pixel.
+//
+// Kernels: per-channel means (shift against cancellation), per-block sums of
+// shifted patch vectors and their products (FP32 within a block, FP64 across
+// blocks), one CTA for the FP64 covariance and its eigendecomposition (cyclic
+// Jacobi in round-robin order: D/2 disjoint rotations per step), and the
+// projection.
+#include <math.h>
+
+#include "hdf_internal.cuh"
+
+namespace hdf {
+namespace {
+
+constexpr int NL_THREADS = 256;
+constexpr int NL_TILE = 16;          // pixels per tile side in the covariance pass
+constexpr int NL_MAXD = 96;          // patch dimension n * patch^2 handled by the FP64 eigen step
+
+__device__ __forceinline__ int mirror(int i, int n) {
+  // reflect without repeating the edge: -1 -> 1, n -> n - 2 (n >= 2)
+  if (i < 0) i = -i;
+  if (i >= n) i = 2 * (n - 1) - i;
+  return i;
+}
+
+// Patch coordinate a = (channel, dy, dx) in channel-major order, as in the oracle.
+__device__ __forceinline__ float patch_val(const float* f, int H, int W, int m, int a, int y, int x) {
+  const int h = m / 2;
+  const int c = a / (m * m), r = a % (m * m);
+  const int yy = mirror(y + r / m - h, H), xx = mirror(x + r % m - h, W);
+  return __ldg(f + (size_t)c * H * W + (size_t)yy * W + xx);
+}
+
+__global__ void nlm_mean_kernel(const float* __restrict__ f, int n, int N, double* part) {
+  __shared__ double red[NL_THREADS];
+  for (int c = 0; c < n; ++c) {
+    float s = 0.0f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+      s += __ldg(f + (size_t)c * N + i);
+    red[threadIdx.x] = (double)s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(size_t)blockIdx.x * n + c] = red[0];
+    __syncthreads();
+  }
+}
+
+// Per block: sum of (X - s) and of (X - s)(X - s)^T (upper triangle) over the
+// block's tiles, s = per-channel mean.
+template <int PER>
+__global__ void __launch_bounds__(NL_THREADS)
+nlm_cov_kernel(const float* __restrict__ f, int n, int H, int W, int m, const double* mean_part,
+               int nblk_mean, float* __restrict__ part) {
+  extern __shared__ float sm[];
+  const int D = n * m * m;
+  const int NP = D * (D + 1) / 2;
+  float* sX = sm;                                   // [D][NL_TILE*NL_TILE] shifted patch values
+  __shared__ float shift[4];
+  if (threadIdx.x < n) {
+    double t = 0.0;
+    for (int b = 0; b < nblk_mean; ++b) t += mean_part[(size_t)b * n + threadIdx.x];
+    shift[threadIdx.x] = (float)(t / ((double)H * W));
+  }
+  __syncthreads();
+  float acc[PER], acc1 = 0.0f;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) acc[j] = 0.0f;
+  int pa[PER], pb[PER];
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    int q = threadIdx.x + j * NL_THREADS, a = 0;
+    if (q >= NP) { pa[j] = -1; pb[j] = -1; continue; }
+    while (q >= D - a) { q -= D - a; ++a; }         // q-th pair of row a: (a, a + q)
+    pa[j] = a;
+    pb[j] = a + q;
+  }
+  const int tiles_x = (W + NL_TILE - 1) / NL_TILE, tiles = tiles_x * ((H + NL_TILE - 1) / NL_TILE);
+  for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int y0 = (t / tiles_x) * NL_TILE, x0 = (t % tiles_x) * NL_TILE;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < D * NL_TILE * NL_TILE; idx += NL_THREADS) {
+      const int a = idx / (NL_TILE * NL_TILE), pix = idx % (NL_TILE * NL_TILE);
+      const int y = y0 + pix / NL_TILE, x = x0 + pix % NL_TILE;
+      float v = 0.0f;
+      if (y < H && x < W) v = patch_val(f, H, W, m, a, y, x) - shift[a / (m * m)];
+      sX[a * NL_TILE * NL_TILE + pix] = v;          // 0 outside the image: contributes nothing
+    }
+    __syncthreads();
+    for (int pix = 0; pix < NL_TILE * NL_TILE; ++pix) {
+#pragma unroll
+      for (int j = 0; j < PER; ++j)
+        if (pa[j] >= 0)
+          acc[j] = fmaf(sX[pa[j] * NL_TILE * NL_TILE + pix], sX[pb[j] * NL_TILE * NL_TILE + pix], acc[j]);
+    }
+    if ((int)threadIdx.x < D)
+      for (int pix = 0; pix < NL_TILE * NL_TILE; ++pix) acc1 += sX[threadIdx.x * NL_TILE * NL_TILE + pix];
+  }
+  float* out = part + (size_t)blockIdx.x * (NP + D);
+#pragma unroll
+  for (int j = 0; j < PER; ++j)
+    if (pa[j] >= 0) out[threadIdx.x + j * NL_THREADS] = acc[j];
+  if ((int)threadIdx.x < D) out[NP + threadIdx.x] = acc1;
+}
+
+// One CTA: covariance in FP64, Jacobi eigendecomposition, top-rho basis.
+__global__ void __launch_bounds__(NL_THREADS)
+nlm_eig_kernel(const float* __restrict__ part, int nblk, int n, int m, int N, int rho,
+               const double* mean_part, int nblk_mean, float* __restrict__ basis,
+               float* __restrict__ pmean, int* ctrl) {
+  extern __shared__ double dm[];
+  const int D = n * m * m, NP = D * (D + 1) / 2;
+  const int DE = D + (D & 1);                       // even size for the round-robin schedule
+  double* A = dm;                                   // DE x DE
+  double* V = A + DE * DE;                          // DE x DE eigenvectors (columns)
+  double* mu = V + DE * DE;                         // D  mean of the shifted patch vectors
+  __shared__ double cs[NL_MAXD / 2 + 1][2];
+  __shared__ int pp[NL_MAXD / 2 + 1], qq[NL_MAXD / 2 + 1];
+  __shared__ double red[NL_THREADS];
+  __shared__ double shift[4];
+  const int tid = threadIdx.x;
+  if (tid < n) {
+    double t = 0.0;
+    for (int b = 0; b < nblk_mean; ++b) t += mean_part[(size_t)b * n + tid];
+    shift[tid] = (double)(float)(t / (double)N);    // the float shift the covariance pass used
+  }
+  for (int a = tid; a < D; a += NL_THREADS) {
+    double t = 0.0;
+    for (int b = 0; b < nblk; ++b) t += (double)part[(size_t)b * (NP + D) + NP + a];
+    mu[a] = t / (double)N;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < DE * DE; idx += NL_THREADS) {
+    const int i = idx / DE, j = idx % DE;
+    double v = 0.0;
+    if (i < D && j < D) {
+      const int a = i < j ? i : j, b = i < j ? j : i;
+      const int q = a * D - a * (a - 1) / 2 + (b - a);  // pair index of (a, b)
+      double t = 0.0;
+      for (int bl = 0; bl < nblk; ++bl) t += (double)part[(size_t)bl * (NP + D) + q];
+      v = t / (double)N - mu[a] * mu[b];
+    }
+    A[idx] = v;
+    V[idx] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int half = DE / 2;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    double off = 0.0, dia = 0.0;
+    for (int idx = tid; idx < DE * DE; idx += NL_THREADS) {
+      const double v = A[idx] * A[idx];
+      if (idx / DE == idx % DE) dia += v; else off += v;
+    }
+    red[tid] = off;
+    __syncthreads();
+    for (int o = NL_THREADS / 2; o > 0; o >>= 1) {
+      if (tid < o) red[tid] += red[tid + o];
+      __syncthreads();
+    }
+    const double off_all = red[0];
+    __syncthreads();
+    red[tid] = dia;
+    __syncthreads();
+    for (int o = NL_THREADS / 2; o > 0; o >>= 1) {
+      if (tid < o) red[tid] += red[tid + o];
+      __syncthreads();
+    }
+    const double dia_all = red[0];
+    __syncthreads();
+    if (off_all <= 1e-30 * dia_all || off_all == 0.0) break;
+    for (int r = 0; r < DE - 1; ++r) {
+      if (tid < half) {   // round-robin pairs: position 0 fixed, the others rotate
+        const int j = tid;
+        auto player = [&](int pos) { return pos == 0 ? 0 : 1 + ((pos - 1 + r) % (DE - 1)); };
+        int p = player(j), q = player(DE - 1 - j);
+        if (p > q) { const int t = p; p = q; q = t; }
+        pp[j] = p;
+        qq[j] = q;
+        double c = 1.0, s = 0.0;
+        const double apq = A[p * DE + q];
+        if (apq != 0.0) {
+          const double tau = (A[q * DE + q] - A[p * DE + p]) / (2.0 * apq);
+          const double t = tau >= 0.0 ? 1.0 / (tau + sqrt(1.0 + tau * tau))
+                                      : -1.0 / (-tau + sqrt(1.0 + tau * tau));
+          c = 1.0 / sqrt(1.0 + t * t);
+          s = t * c;
+        }
+        cs[j][0] = c;
+        cs[j][1] = s;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < DE * half; idx += NL_THREADS) {   // columns p, q of A J and V J
+        const int k = idx / half, j = idx % half;
+        const int p = pp[j], q = qq[j];
+        const double c = cs[j][0], s = cs[j][1];
+        const double ap = A[k * DE + p], aq = A[k * DE + q];
+        A[k * DE + p] = c * ap - s * aq;
+        A[k * DE + q] = s * ap + c * aq;
+        const double vp = V[k * DE + p], vq = V[k * DE + q];
+        V[k * DE + p] = c * vp - s * vq;
+        V[k * DE + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < DE * half; idx += NL_THREADS) {   // rows p, q of J^T (A J)
+        const int j = idx / DE, k = idx % DE;
+        const int p = pp[j], q = qq[j];
+        const double c = cs[j][0], s = cs[j][1];
+        const double ap = A[p * DE + k], aq = A[q * DE + k];
+        A[p * DE + k] = c * ap - s * aq;
+        A[q * DE + k] = s * ap + c * aq;
+      }
+      __syncthreads();
+    }
+  }
+  // the rho largest eigenvalues (ties -> lower index); basis[d][a], mean patch
+  if (tid == 0) {
+    bool used[NL_MAXD];
+    for (int i = 0; i < D; ++i) used[i] = false;
+    for (int d = 0; d < rho; ++d) {
+      int best = -1;
+      for (int i = 0; i < D; ++i)
+        if (!used[i] && (best < 0 || A[i * DE + i] > A[best * DE + best])) best = i;
+      used[best] = true;
+      pp[d] = best;
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < rho * D; idx += NL_THREADS) {
+    const int d = idx / D, a = idx % D;
+    basis[idx] = (float)V[a * DE + pp[d]];
+  }
+  for (int a = tid; a < D; a += NL_THREADS) pmean[a] = (float)(mu[a] + shift[a / (m * m)]);
+  (void)ctrl;
+}
+
+template <int RMAX>
+__global__ void __launch_bounds__(NL_THREADS)
+nlm_project_kernel(const float* __restrict__ f, int n, int H, int W, int m, int rho,
+                   const float* __restrict__ basis, const float* __restrict__ pmean,
+                   float* __restrict__ p) {
+  extern __shared__ float sb[];
+  const int D = n * m * m;
+  float* sbasis = sb;                // rho x D
+  float* smean = sb + rho * D;       // D
+  for (int i = threadIdx.x; i < rho * D; i += blockDim.x) sbasis[i] = basis[i];
+  for (int i = threadIdx.x; i < D; i += blockDim.x) smean[i] = pmean[i];
+  __syncthreads();
+  const size_t N = (size_t)H * W;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (int)N; i += gridDim.x * blockDim.x) {
+    const int y = i / W, x = i % W;
+    float acc[RMAX];
+#pragma unroll
+    for (int d = 0; d < RMAX; ++d) acc[d] = 0.0f;
+    for (int a = 0; a < D; ++a) {
+      const float v = patch_val(f, H, W, m, a, y, x) - smean[a];
+#pragma unroll
+      for (int d = 0; d < RMAX; ++d)
+        if (d < rho) acc[d] = fmaf(sbasis[d * D + a], v, acc[d]);
+    }
+#pragma unroll
+    for (int d = 0; d < RMAX; ++d)
+      if (d < rho) p[(size_t)d * N + i] = acc[d];
+  }
+}
+
+}  // namespace
+
+size_t nlm_workspace_bytes(int G) {
+  const int D = NL_MAXD;
+  return sizeof(float) * (size_t)G * (D * (D + 1) / 2 + D) + sizeof(double) * (size_t)G * 4 +
+         sizeof(float) * (D * HDF_MAX_RHO + D) + 1024;
+}
+
+cudaError_t launch_nlm_guide(const float* f, int n, int H, int W, int m, int rho, float* p,
+                             void* ws, size_t ws_bytes, int* ctrl, cudaStream_t st) {
+  const int D = n * m * m;
+  if (D > NL_MAXD || n > 4 || rho > HDF_MAX_RHO || rho > D || (m & 1) == 0 || H < m / 2 + 1 ||
+      W < m / 2 + 1)
+    return cudaErrorInvalidValue;
+  const int NP = D * (D + 1) / 2;
+  if (NP > 24 * NL_THREADS) return cudaErrorInvalidValue;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int G = sms;
+  if (nlm_workspace_bytes(G) > ws_bytes) return cudaErrorInvalidValue;
+  unsigned char* w = (unsigned char*)ws;
+  float* cov_part = (float*)w;
+  double* mean_part = (double*)(w + sizeof(float) * (size_t)G * (NP + D) + 64 - ((sizeof(float) * (size_t)G * (NP + D)) & 63));
+  float* basis = (float*)(mean_part + (size_t)G * 4);
+  float* pmean = basis + rho * D;
+  const int N = H * W;
+  nlm_mean_kernel<<<G, NL_THREADS, 0, st>>>(f, n, N, mean_part);
+  const size_t smem_cov = sizeof(float) * (size_t)D * NL_TILE * NL_TILE;
+  cudaError_t e;
+  if (NP <= 8 * NL_THREADS) {
+    e = cudaFuncSetAttribute(nlm_cov_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cov);
+    if (e != cudaSuccess) return e;
+    nlm_cov_kernel<8><<<G, NL_THREADS, smem_cov, st>>>(f, n, H, W, m, mean_part, G, cov_part);
+  } else {
+    e = cudaFuncSetAttribute(nlm_cov_kernel<24>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cov);
+    if (e != cudaSuccess) return e;
+    nlm_cov_kernel<24><<<G, NL_THREADS, smem_cov, st>>>(f, n, H, W, m, mean_part, G, cov_part);
+  }
+  const int DE = D + (D & 1);
+  const size_t smem_eig = sizeof(double) * (2 * (size_t)DE * DE + D);
+  e = cudaFuncSetAttribute(nlm_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_eig);
+  if (e != cudaSuccess) return e;
+  nlm_eig_kernel<<<1, NL_THREADS, smem_eig, st>>>(cov_part, G, n, m, N, rho, mean_part, G, basis,
+                                                  pmean, ctrl);
+  const size_t smem_p = sizeof(float) * ((size_t)rho * D + D);
+  if (rho <= 8)
+    nlm_project_kernel<8><<<G * 4, NL_THREADS, smem_p, st>>>(f, n, H, W, m, rho, basis, pmean, p);
+  else
+    nlm_project_kernel<64><<<G * 4, NL_THREADS, smem_p, st>>>(f, n, H, W, m, rho, basis, pmean, p);
+  return cudaGetLastError();
+}
+
+}  // namespace hdf

@@ -1,0 +1,91 @@
+"""GPU backward pass (dL/df, dL/dlog sigma_s, dL/dlog sigma_r with the centres
+and S fixed) against the FP64 autograd reference of oracle/hdfilter_grad.py,
+which is itself pinned by central differences.  Float32 tolerance: the
+gradients are sums of O(K (2S+1)^2) float32 products, so they are compared
+at 1e-3 of their largest magnitude (elementwise) and 1e-3 relative (scalars)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import hdfilter_grad as OG
+from oracle import hdfilter_oracle as O
+from paper_1811_02363_gb300 import synthetic
+
+pytestmark = pytest.mark.gpu
+RTOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1811_02363_gb300 import build
+    build.build()
+    from paper_1811_02363_gb300 import api as A
+    return A
+
+
+def _check(api, f, p, K, ss, sr, seed):
+    rng = np.random.default_rng(seed)
+    guide = f if p is None else p
+    mu = O.bisecting_kmeans(guide.reshape(guide.shape[0], -1).T.astype(np.float64), K)[0].astype(np.float32)
+    G = rng.normal(size=f.shape).astype(np.float32)
+    S = O.window_halfwidth(ss)
+    gf_ref, gls_ref, glr_ref, g_ref = OG.grads(f.astype(np.float64), None if p is None else p.astype(np.float64),
+                                               mu.astype(np.float64), ss, sr, S, G.astype(np.float64))
+    n, H, W = f.shape
+    flt = api.HDFilter(H, W, n, guide.shape[0], mu.shape[0], ss, sr)
+    flt.set_centers(mu)
+    fd = torch.from_numpy(f).cuda()
+    pd = fd if p is None else torch.from_numpy(p).cuda()
+    gf, gls, glr = flt.backward(fd, pd, torch.from_numpy(G).cuda())
+    st = flt.stats()
+    assert st["fallback_pixels"] == 0 and st["device_error"] == 0
+    gf = gf.cpu().numpy()
+    scale = np.abs(gf_ref).max()
+    assert np.max(np.abs(gf - gf_ref)) <= RTOL * scale, np.max(np.abs(gf - gf_ref)) / scale
+    assert abs(float(gls) - gls_ref) <= RTOL * max(abs(gls_ref), 1e-3 * scale), (float(gls), gls_ref)
+    assert abs(float(glr) - glr_ref) <= RTOL * max(abs(glr_ref), 1e-3 * scale), (float(glr), glr_ref)
+    return flt
+
+
+@pytest.mark.parametrize("shape,K,ss,sr", [((3, 40, 36), 5, 1.3, 0.35), ((3, 70, 45), 8, 2.0, 0.3),
+                                          ((5, 33, 29), 6, 1.0, 0.4)])
+def test_backward_guide_is_image(api, shape, K, ss, sr):
+    n, H, W = shape
+    if n == 3:
+        f = synthetic.color_rectangles(H, W, seed=81)
+    else:
+        f = synthetic.hyperspectral_mixture(H, W, bands=n, seed=82)
+    f = np.clip(f + np.random.default_rng(83).normal(0, 0.03, f.shape), 0, 1).astype(np.float32)
+    _check(api, f, None, K, ss, sr, 84)
+
+
+def test_backward_separate_guide(api):
+    f = synthetic.color_rectangles(48, 40, seed=85)
+    p = np.random.default_rng(86).uniform(size=(2, 48, 40)).astype(np.float32)
+    _check(api, f, p, 6, 1.5, 0.3, 87)
+
+
+def test_backward_crop_of_large_workload(api):
+    # 64 x 64 crop of the 2048 x 2048 colour workload: K = 16, sigma_s = 8 (S = 24), sigma_r = 0.15
+    f = synthetic.color_rectangles(2048, 2048, seed=3)[:, 700:764, 900:964].copy()
+    f = np.clip(f + np.random.default_rng(88).normal(0, 0.02, f.shape), 0, 1).astype(np.float32)
+    _check(api, f, None, 16, 8.0, 0.15, 89)
+
+
+def test_autograd_function(api):
+    f = synthetic.color_rectangles(40, 36, seed=90)
+    mu = O.bisecting_kmeans(f.reshape(3, -1).T.astype(np.float64), 5)[0].astype(np.float32)
+    flt = api.HDFilter(40, 36, 3, 3, 5, 1.3, 0.35)
+    flt.set_centers(mu)
+    fd = torch.from_numpy(f).cuda().requires_grad_(True)
+    ls = torch.tensor(math.log(1.3), device="cuda", requires_grad=True)
+    lr = torch.tensor(math.log(0.35), device="cuda", requires_grad=True)
+    g = api.fast_filter(fd, ls, lr, flt)
+    G = torch.from_numpy(np.random.default_rng(91).normal(size=f.shape).astype(np.float32)).cuda()
+    (g * G).sum().backward()
+    gf2, gls2, glr2 = flt.backward(fd.detach(), fd.detach(), G)
+    assert torch.equal(fd.grad, gf2)
+    assert float(ls.grad) == pytest.approx(float(gls2), rel=1e-6)
+    assert float(lr.grad) == pytest.approx(float(glr2), rel=1e-6)

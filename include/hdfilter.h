@@ -202,6 +202,105 @@ hdf_status hdf_get_trace(hdf_handle* h, int64_t* h_events, int cap, int* count, 
  * `stream`.  Returns the recorded device error, if any. */
 hdf_status hdf_get_stats(hdf_handle* h, hdf_stats* out, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Batches.  Many images of different sizes, channel counts, centre counts
+ * and sigmas go through Algorithm 1 together, each stage one launch for the
+ * whole batch: the clustering of every guide in one cooperative launch (the
+ * grid split into groups of blocks, one group per image, sized by the
+ * image's work), one fit launch, one range-map launch, ONE persistent launch
+ * of the fused convolution/combine tiles of all images (a work list of
+ * (image, tile, plane chunk) items, largest first, taken from a global
+ * counter), and one normalisation launch.  The whole run can be captured in
+ * a CUDA graph and replayed.  Tile shapes (planes per item, tile height) are
+ * chosen per (window bucket, plane count) by hdf_batch_tune, which times the
+ * candidates on the bound images.  This is an engineering extension: the
+ * paper filters one image at a time.
+ * ---------------------------------------------------------------------- */
+typedef struct hdf_batch hdf_batch;
+
+enum {
+  HDF_BATCH_GRAPH = 1,          /* capture the run into a CUDA graph on first use, then replay */
+  HDF_BATCH_TIMED = 2,          /* run without a graph, events between stages (get_times) */
+  HDF_BATCH_SKIP_CLUSTER = 4    /* keep every image's centres and A^+ (no clustering, no fit) */
+};
+
+typedef struct {
+  int SB;        /* compiled window bucket (half-width >= S) */
+  int planes;    /* n + 1 planes per centre */
+  int P, TY;     /* planes per work item, tile height (tile width 32) */
+  float ms;      /* best time of the persistent launch over the images of this key */
+  int chosen;    /* 1 for the shape kept */
+} hdf_tile_trial;
+
+typedef struct {
+  int count;               /* images */
+  int graph_state;         /* 0 none yet, 1 captured and replayed, -1 capture failed (eager) */
+  int launches_per_run;    /* kernel launches of one run */
+  int nitems;              /* work items of the persistent tile launch */
+  int ngroups;             /* block groups of the clustering launch */
+  int grid_cluster;        /* blocks of the clustering launch */
+  int grid_tile;           /* blocks of the persistent tile launch */
+  size_t smem_tile;        /* dynamic shared memory of the tile launch, bytes */
+  size_t device_bytes;     /* device memory the batch owns */
+} hdf_batch_info;
+
+/* Validate `count` descriptors (S filled in when 0), plan the clustering
+ * groups and the default tile shapes, and allocate every workspace in one
+ * device arena.  descs[i].guide_dtype selects the guide storage of image i:
+ * with HDF_GUIDE_BF16 and a NULL guide at bind time, the run converts the
+ * image into a bfloat16 guide it owns (guide = image, rho == n).
+ * Synchronous; the only batch call that allocates device memory. */
+hdf_status hdf_batch_create(hdf_batch** out, int count, const hdf_desc* descs);
+
+/* Release the batch (synchronises the device). */
+void hdf_batch_destroy(hdf_batch* b);
+
+/* Bind the caller's device buffers: d_f[i] image (n, H, W) float32;
+ * d_p[i] guide (rho, H, W) in descs[i].guide_dtype, or NULL for guide =
+ * image (rho == n; bfloat16 storage made by the run when the dtype is
+ * HDF_GUIDE_BF16); d_g[i] output (n, H, W), not aliasing d_f[i] / d_p[i].
+ * Host arrays of `count` device pointers.  Writes the device tables
+ * (synchronous) and drops a captured graph. */
+hdf_status hdf_batch_bind(hdf_batch* b, const float* const* d_f, const void* const* d_p,
+                          float* const* d_g);
+
+/* Install K centres for image i (host, K x rho float32) and compute its A^+;
+ * image i is then not clustered by hdf_batch_run.  Synchronous. */
+hdf_status hdf_batch_set_centers(hdf_batch* b, int i, const float* h_mu, int K);
+
+/* One pass of the method over every bound image.  flags: HDF_BATCH_*.
+ * Asynchronous on `stream` (a graph capture, on first use, runs on the host
+ * and launches nothing until the replay).  Device faults (a bounded wait that
+ * gave up) are recorded per image: hdf_batch_get_stats. */
+hdf_status hdf_batch_run(hdf_batch* b, int flags, void* stream);
+
+/* Autotuner: run the batch once, then for every (window bucket, plane count)
+ * present time each compiled tile shape that fits in shared memory on the
+ * persistent launch restricted to those images (best of `reps` runs, CUDA
+ * events) and keep the fastest.  Synchronous; drops a captured graph. */
+hdf_status hdf_batch_tune(hdf_batch* b, int reps, void* stream);
+
+/* Trials of the last hdf_batch_tune (up to cap); *count = trials. */
+hdf_status hdf_batch_get_tuning(hdf_batch* b, hdf_tile_trial* out, int cap, int* count);
+
+/* Force the tile shape of every image of (SB, planes), e.g. from a saved
+ * tuning.  HDF_EINVAL if the shape is not a compiled one or does not fit. */
+hdf_status hdf_batch_set_shape(hdf_batch* b, int SB, int planes, int P, int TY);
+
+/* Stage times (ms) of the last HDF_BATCH_TIMED run, in order: reset,
+ * bfloat16 guides, clustering, fit, range maps, persistent tiles,
+ * normalisation.  Synchronises.  *count = stages written (<= cap). */
+hdf_status hdf_batch_get_times(hdf_batch* b, float* h_ms, int cap, int* count);
+
+/* Centres of image i (room for descs[i].K x rho floats) and K_eff.  Synchronises. */
+hdf_status hdf_batch_get_centers(hdf_batch* b, int i, float* h_mu, int* K_eff);
+
+/* Statistics of image i (as hdf_get_stats).  Synchronises. */
+hdf_status hdf_batch_get_stats(hdf_batch* b, int i, hdf_stats* out);
+
+/* Plan and state of the batch. */
+hdf_status hdf_batch_get_info(hdf_batch* b, hdf_batch_info* out);
+
 /* Human-readable name of a status code. */
 const char* hdf_status_string(hdf_status s);
 

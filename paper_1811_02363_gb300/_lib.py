@@ -27,6 +27,20 @@ class hdf_stats(C.Structure):
                 ("cluster_error", C.c_double)]
 
 
+HDF_BATCH_GRAPH, HDF_BATCH_TIMED, HDF_BATCH_SKIP_CLUSTER = 1, 2, 4
+
+
+class hdf_tile_trial(C.Structure):
+    _fields_ = [("SB", C.c_int), ("planes", C.c_int), ("P", C.c_int), ("TY", C.c_int),
+                ("ms", C.c_float), ("chosen", C.c_int)]
+
+
+class hdf_batch_info(C.Structure):
+    _fields_ = [("count", C.c_int), ("graph_state", C.c_int), ("launches_per_run", C.c_int),
+                ("nitems", C.c_int), ("ngroups", C.c_int), ("grid_cluster", C.c_int),
+                ("grid_tile", C.c_int), ("smem_tile", C.c_size_t), ("device_bytes", C.c_size_t)]
+
+
 # (name, restype, argtypes) of every exported entry point, in header order.
 _P = C.c_void_p
 SIGNATURES = [
@@ -45,6 +59,18 @@ SIGNATURES = [
     ("hdf_bruteforce", C.c_int, [C.POINTER(hdf_desc), _P, _P, _P, _P]),
     ("hdf_get_trace", C.c_int, [_P, _P, C.c_int, C.POINTER(C.c_int), _P]),
     ("hdf_get_stats", C.c_int, [_P, C.POINTER(hdf_stats), _P]),
+    ("hdf_batch_create", C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(hdf_desc)]),
+    ("hdf_batch_destroy", None, [_P]),
+    ("hdf_batch_bind", C.c_int, [_P, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P)]),
+    ("hdf_batch_set_centers", C.c_int, [_P, C.c_int, _P, C.c_int]),
+    ("hdf_batch_run", C.c_int, [_P, C.c_int, _P]),
+    ("hdf_batch_tune", C.c_int, [_P, C.c_int, _P]),
+    ("hdf_batch_get_tuning", C.c_int, [_P, C.POINTER(hdf_tile_trial), C.c_int, C.POINTER(C.c_int)]),
+    ("hdf_batch_set_shape", C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int]),
+    ("hdf_batch_get_times", C.c_int, [_P, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]),
+    ("hdf_batch_get_centers", C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_int)]),
+    ("hdf_batch_get_stats", C.c_int, [_P, C.c_int, C.POINTER(hdf_stats)]),
+    ("hdf_batch_get_info", C.c_int, [_P, C.POINTER(hdf_batch_info)]),
     ("hdf_status_string", C.c_char_p, [C.c_int]),
     ("hdf_last_cuda_error", C.c_char_p, []),
 ]

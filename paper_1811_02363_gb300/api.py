@@ -224,3 +224,120 @@ def fast_filter(f: torch.Tensor, log_sigma_s: torch.Tensor, log_sigma_r: torch.T
     ``flt``.  ``exp(log_sigma_*)`` must equal the filter's sigmas (the handle
     fixes them and S); gradients flow to f, log_sigma_s and log_sigma_r."""
     return _FastFilterFn.apply(f, log_sigma_s, log_sigma_r, flt, guide)
+
+
+class Batch:
+    """Many images through Algorithm 1 together (hdf_batch_*): one launch per
+    stage for the whole batch, one persistent launch for all convolution /
+    combine tiles, CUDA-graph replay, and an autotuner for tile shapes.
+
+    ``specs``: one dict per image with keys H, W, n, K, sigma_s, sigma_r and
+    optionally rho (default n), S, guide_dtype ("f32" / "bf16"), coef.
+    ``bind(fs, gs, ps=None)`` binds CUDA tensors (ps entries None = guide is
+    the image; with guide_dtype "bf16" the run stores it as bfloat16)."""
+
+    def __init__(self, specs):
+        self.specs = [dict(s) for s in specs]
+        descs = (L.hdf_desc * len(specs))()
+        for i, s in enumerate(self.specs):
+            descs[i] = make_desc(s["H"], s["W"], s["n"], s.get("rho", s["n"]), s["K"],
+                                 s["sigma_s"], s["sigma_r"], s.get("S", 0),
+                                 s.get("guide_dtype", "f32"), s.get("coef", "opt"))
+        self.descs = descs
+        self._b = C.c_void_p()
+        L.check(L.lib().hdf_batch_create(C.byref(self._b), len(specs), descs), "hdf_batch_create")
+        self._bound = None
+
+    def close(self) -> None:
+        if self._b:
+            L.lib().hdf_batch_destroy(self._b)
+            self._b = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __len__(self) -> int:
+        return len(self.specs)
+
+    def bind(self, fs, gs, ps=None) -> None:
+        n = len(self.specs)
+        if len(fs) != n or len(gs) != n or (ps is not None and len(ps) != n):
+            raise ValueError("one tensor per image")
+        for i, (f, g) in enumerate(zip(fs, gs)):
+            d = self.descs[i]
+            _check_image(f, f"f[{i}]")
+            _check_image(g, f"g[{i}]")
+            if tuple(f.shape) != (d.n, d.H, d.W) or tuple(g.shape) != (d.n, d.H, d.W):
+                raise ValueError(f"image {i}: expected ({d.n}, {d.H}, {d.W})")
+            p = None if ps is None else ps[i]
+            if p is not None:
+                want = torch.float32 if d.guide_dtype == L.HDF_GUIDE_F32 else torch.bfloat16
+                _check_image(p, f"p[{i}]", want)
+                if tuple(p.shape) != (d.rho, d.H, d.W):
+                    raise ValueError(f"guide {i}: expected ({d.rho}, {d.H}, {d.W})")
+        arr = C.c_void_p * n
+        fa = arr(*[f.data_ptr() for f in fs])
+        ga = arr(*[g.data_ptr() for g in gs])
+        pa = arr(*[(0 if ps is None or ps[i] is None else ps[i].data_ptr()) for i in range(n)])
+        L.check(L.lib().hdf_batch_bind(self._b, fa, pa, ga), "hdf_batch_bind")
+        self._bound = (list(fs), list(gs), None if ps is None else list(ps))   # keep alive
+
+    def set_centers(self, i: int, mu) -> None:
+        d = self.descs[i]
+        mu = np.ascontiguousarray(np.asarray(mu, dtype=np.float32))
+        if mu.ndim != 2 or mu.shape[1] != d.rho:
+            raise ValueError("centres must be (K, rho)")
+        L.check(L.lib().hdf_batch_set_centers(self._b, int(i), mu.ctypes.data_as(C.c_void_p),
+                                              mu.shape[0]), "hdf_batch_set_centers")
+
+    def run(self, graph: bool = True, timed: bool = False, skip_cluster: bool = False) -> None:
+        flags = (L.HDF_BATCH_GRAPH if graph else 0) | (L.HDF_BATCH_TIMED if timed else 0) | \
+            (L.HDF_BATCH_SKIP_CLUSTER if skip_cluster else 0)
+        L.check(L.lib().hdf_batch_run(self._b, flags, _stream()), "hdf_batch_run")
+
+    def tune(self, reps: int = 3) -> list[dict]:
+        L.check(L.lib().hdf_batch_tune(self._b, int(reps), _stream()), "hdf_batch_tune")
+        return self.tuning()
+
+    def tuning(self) -> list[dict]:
+        cnt = C.c_int()
+        L.check(L.lib().hdf_batch_get_tuning(self._b, None, 0, C.byref(cnt)), "get_tuning")
+        arr = (L.hdf_tile_trial * max(1, cnt.value))()
+        L.check(L.lib().hdf_batch_get_tuning(self._b, arr, cnt.value, C.byref(cnt)), "get_tuning")
+        return [{k: getattr(arr[i], k) for k, _ in L.hdf_tile_trial._fields_}
+                for i in range(cnt.value)]
+
+    def set_shape(self, SB: int, planes: int, P: int, TY: int) -> None:
+        L.check(L.lib().hdf_batch_set_shape(self._b, SB, planes, P, TY), "hdf_batch_set_shape")
+
+    def times(self) -> list[float]:
+        """Stage times (ms) of the last timed run: reset, bf16 guides,
+        clustering, fit, range maps, persistent tiles, normalise."""
+        arr = (C.c_float * 7)()
+        cnt = C.c_int()
+        L.check(L.lib().hdf_batch_get_times(self._b, arr, 7, C.byref(cnt)), "get_times")
+        return [arr[i] for i in range(cnt.value)]
+
+    def get_centers(self, i: int) -> np.ndarray:
+        d = self.descs[i]
+        mu = np.zeros((d.K, d.rho), np.float32)
+        k = C.c_int()
+        L.check(L.lib().hdf_batch_get_centers(self._b, int(i), mu.ctypes.data_as(C.c_void_p),
+                                              C.byref(k)), "get_centers")
+        return mu[: k.value].copy()
+
+    def stats(self, i: int) -> dict:
+        s = L.hdf_stats()
+        code = L.lib().hdf_batch_get_stats(self._b, int(i), C.byref(s))
+        d = {k: getattr(s, k) for k, _ in L.hdf_stats._fields_}
+        if code != L.HDF_OK:
+            raise L.HDFError(code, f"device status of image {i}")
+        return d
+
+    def info(self) -> dict:
+        s = L.hdf_batch_info()
+        L.check(L.lib().hdf_batch_get_info(self._b, C.byref(s)), "get_info")
+        return {k: getattr(s, k) for k, _ in L.hdf_batch_info._fields_}

@@ -41,89 +41,9 @@
 
 #include <math.h>
 
-#include "hdf_internal.cuh"
+#include "cluster_args.cuh"
 
 namespace hdf {
-namespace clus {
-
-
-constexpr int CL_THREADS = 256;
-constexpr int CL_WARPS = CL_THREADS / 32;
-constexpr int PPT = 8;                  // points per thread per chunk
-constexpr int CH = CL_THREADS * PPT;    // points per chunk
-constexpr int MAXACT = 32;              // splits per round
-constexpr int MAXSEG = 2 * MAXACT;
-constexpr int MAXNODES = 16 * HDF_MAX_K;
-constexpr int MAX_LLOYD = 20;
-constexpr unsigned long long BARRIER_NS = 2000000000ull;
-constexpr float TIE_REL = 1.0f / 16384.0f;      // 2^-14: Lloyd recheck band
-constexpr float CAND_REL = 1.0f / 4096.0f;      // 2^-12: farthest-point candidates
-constexpr int TRACE_CAP = 2048;                  // trace events per launch
-constexpr float MARGIN_REL = 1.0f / 4096.0f;    // 2^-12: rounding allowance of a stored margin
-constexpr double ROUND_UP = 1.0 + 1.0 / 1048576.0;
-
-// Phases recorded in the trace (one event per grid barrier passed by block 0).
-enum TracePhase { TR_ROOT = 1, TR_DIST1 = 2, TR_DIST2 = 3, TR_NODE = 4, TR_LLOYD = 5,
-                  TR_COUNT = 6, TR_SCATTER = 7, TR_CHILD = 8, TR_LPASS = 9, TR_LREPLAY = 10,
-                  TR_LUPDATE = 11, TR_LPUB = 12 };
-
-// Record a trace event from block 0 outside a barrier.
-__device__ __forceinline__ void trace_event(long long* trace, int phase) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const long long n = trace[0];
-    if (n < TRACE_CAP) {
-      trace[1 + 2 * n] = phase;
-      trace[2 + 2 * n] = (long long)globaltimer_ns();
-      trace[0] = n + 1;
-    }
-  }
-}
-
-struct NodeRec {
-  int start, count;   // segment of the permutation
-  int child0;         // first child (-1: not split); child 2 = child0 + 1
-  int far_idx;        // raster index of the point farthest from the mean
-  double sse;         // sum of squared deviations (0: never split)
-};
-
-struct SlotRec {      // a split in flight (block-local copy, identical in every block)
-  int node, start, count;
-  int a_idx, b_idx;
-  int done, iters, rev_it;   // rev_it: iteration whose changes were undone (-1: none)
-  int cnt_b_cur, cnt_b_acc;
-  int split;          // produces children
-  int recompute;      // centres to be recomputed from the assignment just made
-};
-
-struct ClArgs {
-  const void* p;
-  int p_bf16;         // guide stored as bfloat16
-  int N, rho, K, G;
-  int* ctrl;
-  float* mu;          // out: K x rho
-  double* mu64;       // out: K x rho
-  int32_t* labels;    // out: N
-  double* ek;         // out: E_K
-  uint32_t* perm;     // N
-  uint32_t* perm2;    // N
-  float* X;           // rho x N points in permutation order
-  float* X2;          // rho x N scatter target
-  uint8_t* side;      // 2 x N
-  float* marg;        // N margin bound + total centre movement when it was computed
-  float* d32;         // N
-  NodeRec* nodes;     // MAXNODES
-  double* node_sum;   // MAXNODES x rho coordinate sums
-  float* pf;          // G x MAXSEG x (rho + 1) double-float pairs
-  int* pi;            // G x MAXSEG x 2
-  float* pd;          // G x MAXSEG
-  double* pdd;        // G x MAXSEG
-  int* px;            // G x MAXSEG
-  int* chunk_cnt;     // max chunks
-  long long* trace;   // [0] = count, then (phase, ns) pairs, block 0 only
-  double* fin;        // MAXACT x (rho + 2) reduced Lloyd sums, published by the owner blocks
-};
-
-}  // namespace clus
 
 namespace clus {
 namespace {
@@ -187,7 +107,7 @@ __device__ bool grid_barrier(const ClArgs& a, unsigned& gen, ClShared& s, int ph
     __threadfence();
     ++gen;
     s.ok = (*(volatile int*)(a.ctrl + CTRL_ERROR) == 0);
-    if (blockIdx.x == 0) {
+    if (a.bid == 0) {
       const long long n = a.trace[0];
       if (n < TRACE_CAP) {
         a.trace[1 + 2 * n] = phase;
@@ -327,7 +247,7 @@ __device__ void replay(int nvals, T init, NC nc_of, SRC src, COMB combine, DST d
 template <class F, class Flush>
 __device__ void for_blocks(const ClArgs& a, const ClShared& s, F f, Flush flush) {
   int cur = -1, seg = 0;
-  for (int j = blockIdx.x; j < s.nchunks; j += a.G) {
+  for (int j = a.bid; j < s.nchunks; j += a.G) {
     while (s.seg_chunk0[seg + 1] <= j) ++seg;
     if (seg != cur) {
       if (cur >= 0) flush(cur);
@@ -578,11 +498,9 @@ __host__ __device__ constexpr size_t dyn_smem_bytes(int rho) {
                                                  3 * (size_t)MAXACT * rho);
 }
 
+// The clustering of one guide by the blocks of its group.
 template <int RMAX>
-__global__ void __launch_bounds__(CL_THREADS, 1)
-cluster_kernel(const ClArgs a) {
-  __shared__ ClShared s;
-  extern __shared__ __align__(16) unsigned char dyn[];
+__device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
   const int rho = a.rho;
   const int PS = 2 * (rho + 1);   // floats per partial record (pairs)
   float* c32 = (float*)dyn;                                   // MAXSEG x rho
@@ -593,7 +511,7 @@ cluster_kernel(const ClArgs a) {
   double* mean_a = nsum + MAXACT * rho;                       // MAXACT x rho
   auto acc_sum_a = [&](int i, int d) -> double& { return mean_a[i * rho + d]; };
   unsigned gen = 0;
-  const int tid = threadIdx.x, bid = blockIdx.x;
+  const int tid = threadIdx.x, bid = a.bid;
   const size_t N = (size_t)a.N;
   int nnodes = 1, rounds = 0, lloyd_max = 0;
   // points whose coordinates are loaded together (registers permitting)
@@ -1006,7 +924,7 @@ cluster_kernel(const ClArgs a) {
               chg = 0;
             });
       }
-      trace_event(a.trace, TR_LPASS);
+      trace_event(a.trace, a.bid, TR_LPASS);
       if (!grid_barrier(a, gen, s, TR_LLOYD)) return;
       // replay the reduction of every active split: side-b sums, count, changes
       // Each split's partial sums are reduced by its owner block (split i ->
@@ -1033,7 +951,7 @@ cluster_kernel(const ClArgs a) {
       for (int v = tid; v < s.nslots * (rho + 2); v += CL_THREADS)
         tmp[v] = s.slot[v / (rho + 2)].done ? 0.0 : __ldcg(a.fin + v);
       __syncthreads();
-      trace_event(a.trace, TR_LREPLAY);
+      trace_event(a.trace, a.bid, TR_LREPLAY);
       for (int i = tid; i < s.nslots; i += CL_THREADS) {
         {
           SlotRec& sl = s.slot[i];
@@ -1125,7 +1043,7 @@ cluster_kernel(const ClArgs a) {
       }
       __syncthreads();
       build_chunks(s);
-      trace_event(a.trace, TR_LUPDATE);
+      trace_event(a.trace, a.bid, TR_LUPDATE);
     }
     if (tid == 0) {
       for (int i = 0; i < s.nslots; ++i) {
@@ -1344,22 +1262,65 @@ cluster_kernel(const ClArgs a) {
 }
 
 
-// Host: cooperative launch of one instantiation.
+// One cooperative launch clusters a table of guides.  The grid is split into
+// groups of consecutive blocks, groups[g] = (first block, block count, first
+// and one-past-last entry of `order`); the group clusters the guides
+// order[z..w) one after the other, each with its own control words (grid
+// barrier counters) and workspace, so groups never wait on one another.
+// p_override (if not null) replaces the guide pointer of every entry.
 template <int RMAX>
-cudaError_t launch_cl(const ClArgs& a, int G, cudaStream_t st) {
-  const size_t smem = dyn_smem_bytes(a.rho);
+__global__ void __launch_bounds__(CL_THREADS, 1)
+cluster_kernel(const ClArgs* __restrict__ table, const int4* __restrict__ groups, int ngroups,
+               const int* __restrict__ order, const void* p_override) {
+  __shared__ ClShared s;
+  __shared__ ClArgs sa;
+  __shared__ int4 s_grp;
+  extern __shared__ __align__(16) unsigned char dyn[];
+  if (threadIdx.x == 0) {
+    s_grp = make_int4(0, 0, 0, 0);
+    for (int g = 0; g < ngroups; ++g) {
+      const int4 gr = groups[g];
+      if ((int)blockIdx.x >= gr.x && (int)blockIdx.x < gr.x + gr.y) s_grp = gr;
+    }
+  }
+  __syncthreads();
+  const int4 gr = s_grp;
+  for (int t = gr.z; t < gr.w; ++t) {
+    if (threadIdx.x == 0) {
+      sa = table[order[t]];
+      sa.bid = (int)blockIdx.x - gr.x;
+      if (p_override) sa.p = p_override;
+    }
+    __syncthreads();
+    cluster_run<RMAX>(sa, s, dyn);
+    __syncthreads();
+  }
+}
+
+// Host: cooperative launch of one instantiation over `grid` blocks.
+template <int RMAX>
+cudaError_t launch_cl(const ClArgs* table, const int4* groups, int ngroups, const int* order,
+                      const void* p_override, int rho_max, int grid, cudaStream_t st) {
+  const size_t smem = dyn_smem_bytes(rho_max);
   cudaError_t e = cudaFuncSetAttribute(cluster_kernel<RMAX>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  int dev = 0, occ = 0;
-  cudaGetDevice(&dev);
+  int occ = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cluster_kernel<RMAX>, CL_THREADS,
                                                     smem);
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorCooperativeLaunchTooLarge;
-  void* args[] = {(void*)&a};
-  return cudaLaunchCooperativeKernel((const void*)cluster_kernel<RMAX>, dim3(G),
-                                     dim3(CL_THREADS), args, smem, st);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(CL_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, cluster_kernel<RMAX>, table, groups, ngroups, order, p_override);
 }
 
 }  // namespace

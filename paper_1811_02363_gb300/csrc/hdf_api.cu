@@ -10,19 +10,15 @@
 #include "hdf_internal.cuh"
 
 namespace {
-
 thread_local char g_cuda_err[256] = "";
+}  // namespace
+
+namespace hdf {
 
 hdf_status cuda_fail(cudaError_t e, const char* where) {
   snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", where, cudaGetErrorString(e));
   return HDF_ECUDA;
 }
-
-#define HDF_CUDA(call, where)                       \
-  do {                                              \
-    cudaError_t e_ = (call);                        \
-    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
-  } while (0)
 
 hdf_status check_desc(hdf_desc* d) {
   if (!d) return HDF_EINVAL;
@@ -39,6 +35,13 @@ hdf_status check_desc(hdf_desc* d) {
   if ((long long)d->H * d->W >= (1LL << 31)) return HDF_EUNSUPPORTED;
   return HDF_OK;
 }
+
+}  // namespace hdf
+
+namespace {
+
+using hdf::check_desc;
+using hdf::cuda_fail;
 
 template <class T>
 cudaError_t dalloc(T** p, size_t count) {
@@ -124,7 +127,7 @@ hdf_status hdf_create(hdf_handle** out, const hdf_desc* desc) {
   if (cudaMemset(h->ctrl, 0, hdf::CTRL_WORDS * sizeof(int)) != cudaSuccess ||
       cudaMemset(h->mu, 0, K * R * sizeof(float)) != cudaSuccess ||
       cudaMemset(h->ek, 0, sizeof(double)) != cudaSuccess ||
-      cudaDeviceSynchronize() != cudaSuccess) {
+      hdf::cluster_init(h) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
     hdf_destroy(h);
     return cuda_fail(cudaGetLastError(), "hdf_create init");
   }

@@ -82,13 +82,25 @@ struct hdf_handle {
 
 namespace hdf {
 
+// One fit (A and A^+ of one image's centres) of a batch.
+struct FitJob {
+  const float* mu;
+  int rho;
+  int* ctrl;
+  double inv2sr2;
+  double* pinv64;
+  float* pinv32;
+};
+
 // Launchers (each returns cudaGetLastError() of its launch).
 cudaError_t launch_fit(hdf_handle* h, cudaStream_t st);           // A, A^+ from h->mu
+cudaError_t launch_fit_batch(const FitJob* jobs, int njobs, int Kmax, cudaStream_t st);
 cudaError_t launch_set_int(int* p, int v, cudaStream_t st);
 cudaError_t launch_rangemap(hdf_handle* h, const void* p, cudaStream_t st);
 cudaError_t launch_filter(hdf_handle* h, const float* f, float* g, cudaStream_t st);
 cudaError_t launch_bruteforce(const hdf_desc& d, const float* f, const void* p, float* g,
                               cudaStream_t st);
+cudaError_t cluster_init(hdf_handle* h);                          // one-entry table, at create
 cudaError_t launch_cluster(hdf_handle* h, const void* p, cudaStream_t st);
 size_t cluster_workspace_bytes(int N, int rho, int K);
 size_t nlm_workspace_bytes(int G);
@@ -100,5 +112,15 @@ cudaError_t launch_backward(hdf_handle* h, const float* f, const void* p, const 
 
 // Host helpers.
 Taps make_taps(double sigma_s, int S);
+hdf_status cuda_fail(cudaError_t e, const char* where);   // records the text for hdf_last_cuda_error
+hdf_status check_desc(hdf_desc* d);                       // validates, fills S = ceil(3 sigma_s) if 0
+int filter_bucket(int S);                                 // compiled window bucket >= S, -1 if none
 
 }  // namespace hdf
+
+// Return HDF_ECUDA (with the error text recorded) if a CUDA call fails.
+#define HDF_CUDA(call, where)                                  \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return hdf::cuda_fail(e_, where);   \
+  } while (0)

@@ -1,32 +1,30 @@
 // Host side of the clustering stage (Algorithm 1 "cluster", Sec. II-C):
 // workspace layout, grid size and dispatch to the per-dimension
 // instantiations of the cooperative kernel (cluster_kernel.cuh), which are
-// compiled in separate translation units.
-#include "cluster_kernel.cuh"
+// compiled in separate translation units.  One launch clusters a table of
+// guides (one entry for a handle, one per image for a batch).
+#include "cluster_args.cuh"
 
 namespace hdf {
 
-cudaError_t launch_cluster_r4(const clus::ClArgs&, int, cudaStream_t);
-cudaError_t launch_cluster_r8(const clus::ClArgs&, int, cudaStream_t);
-cudaError_t launch_cluster_r16(const clus::ClArgs&, int, cudaStream_t);
-cudaError_t launch_cluster_r32(const clus::ClArgs&, int, cudaStream_t);
-cudaError_t launch_cluster_r64(const clus::ClArgs&, int, cudaStream_t);
+cudaError_t launch_cluster_r4(const clus::ClArgs*, const int4*, int, const int*, const void*, int,
+                              int, cudaStream_t);
+cudaError_t launch_cluster_r8(const clus::ClArgs*, const int4*, int, const int*, const void*, int,
+                              int, cudaStream_t);
+cudaError_t launch_cluster_r16(const clus::ClArgs*, const int4*, int, const int*, const void*,
+                               int, int, cudaStream_t);
+cudaError_t launch_cluster_r32(const clus::ClArgs*, const int4*, int, const int*, const void*,
+                               int, int, cudaStream_t);
+cudaError_t launch_cluster_r64(const clus::ClArgs*, const int4*, int, const int*, const void*,
+                               int, int, cudaStream_t);
 
+namespace clus {
 namespace {
-using namespace clus;
-
-// ---------------------------------------------------------------- host side
 
 struct Layout {
   size_t perm, perm2, X, X2, side, marg, d32, nodes, node_sum, pf, pi, pd, pdd, px, chunk_cnt, trace, fin,
-      total;
+      tab, grp, ord, total;
 };
-
-int grid_blocks(int dev) {
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return sms > 0 ? sms : 1;   // one block per SM (co-residency of a cooperative launch)
-}
 
 Layout layout(int N, int rho, int G) {
   Layout L;
@@ -54,37 +52,40 @@ Layout layout(int N, int rho, int G) {
   L.chunk_cnt = take(sizeof(int) * maxchunks);
   L.trace = take(sizeof(long long) * (1 + 2 * TRACE_CAP));
   L.fin = take(sizeof(double) * MAXACT * (size_t)(rho + 2));
+  L.tab = take(sizeof(ClArgs));
+  L.grp = take(sizeof(int4));
+  L.ord = take(sizeof(int));
   L.total = o;
   return L;
 }
 
 }  // namespace
 
-size_t cluster_workspace_bytes(int N, int rho, int K) {
-  (void)K;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  return layout(N, rho, grid_blocks(dev)).total;
+int grid_blocks(int dev) {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;   // one block per SM (co-residency of a cooperative launch)
 }
 
-cudaError_t launch_cluster(hdf_handle* h, const void* p, cudaStream_t st) {
-  int dev = 0;
-  cudaGetDevice(&dev);
-  const int G = grid_blocks(dev);
-  const Layout L = layout(h->N, h->d.rho, G);
-  if (L.total > h->cl_ws_bytes) return cudaErrorInvalidValue;
-  unsigned char* w = (unsigned char*)h->cl_ws;
+size_t ws_bytes(int N, int rho, int G) { return layout(N, rho, G).total; }
+
+ClArgs make_args(void* ws, int N, int rho, int K, int G, int* ctrl, float* mu, double* mu64,
+                 int32_t* labels, double* ek, const void* p, int p_bf16) {
+  const Layout L = layout(N, rho, G);
+  unsigned char* w = (unsigned char*)ws;
   ClArgs a;
   a.p = p;
-  a.N = h->N;
-  a.rho = h->d.rho;
-  a.K = h->d.K;
+  a.p_bf16 = p_bf16;
+  a.N = N;
+  a.rho = rho;
+  a.K = K;
   a.G = G;
-  a.ctrl = h->ctrl;
-  a.mu = h->mu;
-  a.mu64 = h->mu64;
-  a.labels = h->labels;
-  a.ek = h->ek;
+  a.bid = 0;
+  a.ctrl = ctrl;
+  a.mu = mu;
+  a.mu64 = mu64;
+  a.labels = labels;
+  a.ek = ek;
   a.perm = (uint32_t*)(w + L.perm);
   a.perm2 = (uint32_t*)(w + L.perm2);
   a.X = (float*)(w + L.X);
@@ -102,23 +103,71 @@ cudaError_t launch_cluster(hdf_handle* h, const void* p, cudaStream_t st) {
   a.chunk_cnt = (int*)(w + L.chunk_cnt);
   a.trace = (long long*)(w + L.trace);
   a.fin = (double*)(w + L.fin);
-  // barrier words start from zero for every launch
+  return a;
+}
+
+cudaError_t launch_table(int rho_max, const ClArgs* table, const int4* groups, int ngroups,
+                         const int* order, const void* p_override, int grid, cudaStream_t st) {
+  if (rho_max <= 4)
+    return launch_cluster_r4(table, groups, ngroups, order, p_override, rho_max, grid, st);
+  if (rho_max <= 8)
+    return launch_cluster_r8(table, groups, ngroups, order, p_override, rho_max, grid, st);
+  if (rho_max <= 16)
+    return launch_cluster_r16(table, groups, ngroups, order, p_override, rho_max, grid, st);
+  if (rho_max <= 32)
+    return launch_cluster_r32(table, groups, ngroups, order, p_override, rho_max, grid, st);
+  return launch_cluster_r64(table, groups, ngroups, order, p_override, rho_max, grid, st);
+}
+
+}  // namespace clus
+
+size_t cluster_workspace_bytes(int N, int rho, int K) {
+  (void)K;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return clus::ws_bytes(N, rho, clus::grid_blocks(dev));
+}
+
+// The one-entry table of a handle (all blocks in one group), written once at
+// create time; the guide pointer is passed with every launch.
+cudaError_t cluster_init(hdf_handle* h) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int G = clus::grid_blocks(dev);
+  const clus::Layout L = clus::layout(h->N, h->d.rho, G);
+  if (L.total > h->cl_ws_bytes) return cudaErrorInvalidValue;
+  unsigned char* w = (unsigned char*)h->cl_ws;
+  const clus::ClArgs a = clus::make_args(h->cl_ws, h->N, h->d.rho, h->d.K, G, h->ctrl, h->mu,
+                                         h->mu64, h->labels, h->ek, nullptr,
+                                         h->d.guide_dtype == HDF_GUIDE_BF16 ? 1 : 0);
+  const int4 grp = make_int4(0, G, 0, 1);
+  const int ord = 0;
+  cudaError_t e = cudaMemcpy(w + L.tab, &a, sizeof(a), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(w + L.grp, &grp, sizeof(grp), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(w + L.ord, &ord, sizeof(ord), cudaMemcpyHostToDevice);
+  return e;
+}
+
+cudaError_t launch_cluster(hdf_handle* h, const void* p, cudaStream_t st) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int G = clus::grid_blocks(dev);
+  const clus::Layout L = clus::layout(h->N, h->d.rho, G);
+  if (L.total > h->cl_ws_bytes) return cudaErrorInvalidValue;
+  unsigned char* w = (unsigned char*)h->cl_ws;
+  // barrier words and the trace count start from zero for every launch
   cudaError_t e = cudaMemsetAsync(h->ctrl + CTRL_BARRIER, 0, 2 * sizeof(int), st);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(a.trace, 0, sizeof(long long), st);
+  e = cudaMemsetAsync(w + L.trace, 0, sizeof(long long), st);
   if (e != cudaSuccess) return e;
-  a.p_bf16 = h->d.guide_dtype == HDF_GUIDE_BF16 ? 1 : 0;
-  if (a.rho <= 4) return launch_cluster_r4(a, G, st);
-  if (a.rho <= 8) return launch_cluster_r8(a, G, st);
-  if (a.rho <= 16) return launch_cluster_r16(a, G, st);
-  if (a.rho <= 32) return launch_cluster_r32(a, G, st);
-  return launch_cluster_r64(a, G, st);
+  return clus::launch_table(h->d.rho, (const clus::ClArgs*)(w + L.tab),
+                            (const int4*)(w + L.grp), 1, (const int*)(w + L.ord), p, G, st);
 }
 
 cudaError_t cluster_trace(hdf_handle* h, long long* host, int cap, int* count, cudaStream_t st) {
   int dev = 0;
   cudaGetDevice(&dev);
-  const Layout L = layout(h->N, h->d.rho, grid_blocks(dev));
+  const clus::Layout L = clus::layout(h->N, h->d.rho, clus::grid_blocks(dev));
   const long long* t = (const long long*)((unsigned char*)h->cl_ws + L.trace);
   long long n = 0;
   cudaError_t e = cudaMemcpyAsync(&n, t, sizeof(n), cudaMemcpyDeviceToHost, st);

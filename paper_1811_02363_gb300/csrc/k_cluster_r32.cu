@@ -3,8 +3,10 @@
 
 namespace hdf {
 
-cudaError_t launch_cluster_r32(const clus::ClArgs& a, int G, cudaStream_t st) {
-  return clus::launch_cl<32>(a, G, st);
+cudaError_t launch_cluster_r32(const clus::ClArgs* table, const int4* groups, int ngroups,
+                              const int* order, const void* p_override, int rho_max, int grid,
+                              cudaStream_t st) {
+  return clus::launch_cl<32>(table, groups, ngroups, order, p_override, rho_max, grid, st);
 }
 
 }  // namespace hdf

@@ -3,19 +3,16 @@
 // kernel (filter_tile.cuh) for hdf_apply.
 #include <math.h>
 
+#include "combine.cuh"
 #include "filter_tile.cuh"
 #include "hdf_internal.cuh"
 
 namespace hdf {
 namespace {
 
-constexpr float kGuardRel = 1e-6f;   // guard: sum_k c_k r_k <= 1e-6 max_k r_k
-
 constexpr int RM_THREADS = 256;
 
-// b_k(i) = phi(mu_k - p(i)) (Eq. (12)), computed from direct differences in
-// FP32; c(i) = A^+ b(i) (Eq. (11)) or e_s (Eq. (17)); s(i) = nearest centre
-// (ties -> lowest k).
+// Range maps and coefficients of every pixel (combine.cuh).
 template <int KMAX, typename GT>
 __global__ void __launch_bounds__(RM_THREADS)
 rangemap_kernel(const GT* __restrict__ p, int N, int rho, const float* __restrict__ mu,
@@ -31,46 +28,7 @@ rangemap_kernel(const GT* __restrict__ p, int N, int rho, const float* __restric
   __syncthreads();
   const int pix = blockIdx.x * blockDim.x + threadIdx.x;
   if (pix >= N) return;
-  float d2[KMAX];
-#pragma unroll
-  for (int k = 0; k < KMAX; ++k) d2[k] = 0.0f;
-  for (int d = 0; d < rho; ++d) {
-    const float x = guide_load(p, (size_t)d * N + pix);
-#pragma unroll
-    for (int k = 0; k < KMAX; ++k) {
-      if (k < K) {
-        const float t = x - smu[k * rho + d];
-        d2[k] = fmaf(t, t, d2[k]);
-      }
-    }
-  }
-  int s = 0;
-  float best = d2[0];
-#pragma unroll
-  for (int k = 1; k < KMAX; ++k)
-    if (k < K && d2[k] < best) { best = d2[k]; s = k; }
-  float b[KMAX];
-#pragma unroll
-  for (int k = 0; k < KMAX; ++k) b[k] = (k < K) ? expf(-d2[k] * inv2sr2) : 0.0f;
-#pragma unroll
-  for (int k = 0; k < KMAX; ++k)
-    if (k < K) B[(size_t)k * N + pix] = b[k];
-#pragma unroll
-  for (int k = 0; k < KMAX; ++k) {
-    if (k < K) {
-      float c;
-      if (coef == HDF_COEF_OPT) {
-        c = 0.0f;
-#pragma unroll
-        for (int l = 0; l < KMAX; ++l)
-          if (l < K) c = fmaf(spi[k * K + l], b[l], c);
-      } else {
-        c = (k == s) ? 1.0f : 0.0f;
-      }
-      C[(size_t)k * N + pix] = c;
-    }
-  }
-  s_out[pix] = (uint8_t)s;
+  rangemap_pixel<KMAX>(p, (size_t)N, (size_t)pix, rho, K, smu, spi, inv2sr2, coef, B, C, s_out);
 }
 
 template <int KMAX>
@@ -90,9 +48,8 @@ cudaError_t launch_rm(hdf_handle* h, const void* p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// Pixels where the denominator guard fired take the indicator value
-// v_s(i) / r_s(i) of Eq. (18) (s = nearest centre), computed here by direct
-// sums over the window from the stored b_s plane; f(i) if r_s(i) = 0.
+// Pixels where the denominator guard fired take the indicator value of
+// Eq. (18) (combine.cuh).
 __global__ void fixup_kernel(const float* __restrict__ f, const float* __restrict__ B,
                              const uint8_t* __restrict__ s, const int* __restrict__ fix_list,
                              const int* __restrict__ ctrl, int H, int W, int n, int S,
@@ -105,40 +62,17 @@ __global__ void fixup_kernel(const float* __restrict__ f, const float* __restric
        item += (long long)gridDim.x * blockDim.x) {
     const int idx = (int)(item / n), ch = (int)(item % n);
     const int pix = fix_list[idx];
-    const int y = pix / W, x = pix % W;
-    const float* Bs = B + (size_t)s[pix] * N;
-    const float* fc = f + (size_t)ch * N;
-    float r = 0.0f, v = 0.0f;
-    for (int j1 = -S; j1 <= S; ++j1) {
-      const int yy = y - j1;
-      if (yy < 0 || yy >= H) continue;
-      for (int j2 = -S; j2 <= S; ++j2) {
-        const int xx = x - j2;
-        if (xx < 0 || xx >= W) continue;
-        const float w = taps.w[j1 + S] * taps.w[j2 + S] * Bs[(size_t)yy * W + xx];
-        r += w;
-        v = fmaf(w, fc[(size_t)yy * W + xx], v);
-      }
-    }
-    g[(size_t)ch * N + pix] = (r > 0.0f) ? v / r : fc[pix];
+    g[(size_t)ch * N + pix] =
+        fixup_value(f, B, s, H, W, S, [&](int j) { return taps.w[j + S]; }, pix, ch);
   }
 }
 
-// Eq. (15)-(16): g_hat = (sum_k c_k v_k) / (sum_k c_k r_k) per pixel, with the
-// denominator guard; guarded pixels are listed for the indicator fix-up.
+// Eq. (15)-(16) normalisation with the denominator guard (combine.cuh).
 __global__ void divide_kernel(float* __restrict__ g, const float* __restrict__ den,
                               const float* __restrict__ rmax, int* __restrict__ ctrl,
                               int* __restrict__ fix_list, int N, int n) {
-  for (int pix = blockIdx.x * blockDim.x + threadIdx.x; pix < N; pix += gridDim.x * blockDim.x) {
-    const float D = den[pix];
-    if (!(D > kGuardRel * rmax[pix])) {
-      const int pos = atomicAdd(ctrl + CTRL_FALLBACK, 1);
-      if (pos < N) fix_list[pos] = pix;
-      continue;
-    }
-    const float inv = 1.0f / D;
-    for (int c = 0; c < n; ++c) g[(size_t)c * N + pix] *= inv;
-  }
+  for (int pix = blockIdx.x * blockDim.x + threadIdx.x; pix < N; pix += gridDim.x * blockDim.x)
+    divide_pixel(g, den, rmax, ctrl, fix_list, N, n, pix);
 }
 
 }  // namespace

@@ -29,10 +29,8 @@ __device__ double matlab_tol(double norm2, int K) {
   return (double)K * ldexp(1.0, e - 53);
 }
 
-__global__ void __launch_bounds__(FIT_THREADS)
-fit_kernel(const float* __restrict__ mu, int rho, int* ctrl, double inv2sr2,
-           double* __restrict__ pinv64, float* __restrict__ pinv32) {
-  extern __shared__ double sm[];
+__device__ void fit_run(const float* __restrict__ mu, int rho, int* ctrl, double inv2sr2,
+                        double* __restrict__ pinv64, float* __restrict__ pinv32, double* sm) {
   const int K = ctrl[CTRL_K_EFF];
   const int tid = threadIdx.x, nt = blockDim.x;
   double* A = sm;              // K x K
@@ -204,6 +202,21 @@ fit_kernel(const float* __restrict__ mu, int rho, int* ctrl, double inv2sr2,
   for (int idx = tid; idx < K * K; idx += nt) pinv32[idx] = (float)pinv64[idx];
 }
 
+__global__ void __launch_bounds__(FIT_THREADS)
+fit_kernel(const float* __restrict__ mu, int rho, int* ctrl, double inv2sr2,
+           double* __restrict__ pinv64, float* __restrict__ pinv32) {
+  extern __shared__ double sm[];
+  fit_run(mu, rho, ctrl, inv2sr2, pinv64, pinv32, sm);
+}
+
+// One block per entry of a batch table.
+__global__ void __launch_bounds__(FIT_THREADS)
+fit_batch_kernel(const FitJob* __restrict__ jobs) {
+  extern __shared__ double sm[];
+  const FitJob j = jobs[blockIdx.x];
+  fit_run(j.mu, j.rho, j.ctrl, j.inv2sr2, j.pinv64, j.pinv32, sm);
+}
+
 __global__ void set_int_kernel(int* p, int v) { *p = v; }
 
 }  // namespace
@@ -219,6 +232,18 @@ cudaError_t launch_fit(hdf_handle* h, cudaStream_t st) {
   const double inv2sr2 = 1.0 / (2.0 * h->d.sigma_r * h->d.sigma_r);
   fit_kernel<<<1, FIT_THREADS, smem, st>>>(h->mu, h->d.rho, h->ctrl, inv2sr2, h->pinv64,
                                            h->pinv32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fit_batch(const FitJob* jobs, int njobs, int Kmax, cudaStream_t st) {
+  if (njobs < 1) return cudaSuccess;
+  const size_t smem = 3 * (size_t)Kmax * Kmax * sizeof(double);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(fit_batch_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  fit_batch_kernel<<<njobs, FIT_THREADS, smem, st>>>(jobs);
   return cudaGetLastError();
 }
 

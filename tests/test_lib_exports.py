@@ -53,3 +53,24 @@ def test_argument_errors_without_device_work(L):
     assert lib.hdf_bruteforce(C.byref(d), None, None, None, None) == L.HDF_EINVAL
     assert lib.hdf_apply(None, None, None, None, None) == L.HDF_EINVAL
     assert lib.hdf_status_string(L.HDF_ETIMEOUT).startswith(b"HDF_ETIMEOUT")
+
+
+def test_batch_argument_errors_without_device_work(L):
+    lib = L.lib()
+    d = (L.hdf_desc * 2)()
+    for i in range(2):
+        d[i] = L.hdf_desc(H=8 + i, W=8, n=3, rho=3, K=4, S=0, sigma_s=1.0, sigma_r=0.1,
+                          guide_dtype=0, coef=0)
+    b = C.c_void_p()
+    assert lib.hdf_batch_create(C.byref(b), 0, d) == L.HDF_EINVAL
+    assert lib.hdf_batch_create(C.byref(b), 2, None) == L.HDF_EINVAL
+    d[1].sigma_s = 0.0
+    assert lib.hdf_batch_create(C.byref(b), 2, d) == L.HDF_EINVAL
+    d[1].sigma_s = 1.0
+    d[1].S = L.HDF_MAX_S + 1
+    assert lib.hdf_batch_create(C.byref(b), 2, d) == L.HDF_EUNSUPPORTED
+    assert lib.hdf_batch_run(None, 0, None) == L.HDF_EINVAL
+    assert lib.hdf_batch_bind(None, None, None, None) == L.HDF_EINVAL
+    assert lib.hdf_batch_tune(None, 3, None) == L.HDF_EINVAL
+    assert lib.hdf_batch_get_info(None, None) == L.HDF_EINVAL
+

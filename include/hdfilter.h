@@ -190,12 +190,14 @@ hdf_status hdf_bruteforce(const hdf_desc* desc, const float* d_f, const void* d_
                           float* d_g, void* stream);
 
 /* Phase trace of the last hdf_cluster: up to `cap` events, each two int64
- * (phase id, device globaltimer in ns) recorded by block 0 at every grid
- * barrier of the clustering kernel.  Phase ids: 1 root sums, 2 distance
- * pass, 3 farthest-point pass, 4 root node, 5 Lloyd iteration, 6 partition
- * count, 7 partition scatter, 8 children written.  h_events: host, room for
- * 2*cap int64.  *count = events written.  Synchronises `stream`.  Tracing
- * support; not part of the paper's method. */
+ * (phase id, device globaltimer in ns) recorded by block 0 of the clustering
+ * kernel (at most 2048).  Phase ids at the grid barriers: 1 root sums, 2
+ * distance and farthest-point pass, 4 root node, 5 Lloyd iteration, 6
+ * partition count, 7 partition scatter, 8 children written; between them:
+ * 9 end of block 0's Lloyd pass, 11 Lloyd state reloaded, 12-14 block 0
+ * finishing a split (all partial sums arrived, reduced, update published).
+ * h_events: host, room for 2*cap int64.  *count = events written.
+ * Synchronises `stream`.  Tracing support; not part of the paper's method. */
 hdf_status hdf_get_trace(hdf_handle* h, int64_t* h_events, int cap, int* count, void* stream);
 
 /* Statistics and the device status word (see hdf_stats).  Synchronises

@@ -15,6 +15,7 @@ constexpr int MAXACT = 32;              // splits per round
 constexpr int MAXSEG = 2 * MAXACT;
 constexpr int MAXNODES = 16 * HDF_MAX_K;
 constexpr int MAX_LLOYD = 20;
+constexpr int MAXG = 160;               // blocks of one group (one per SM)
 constexpr unsigned long long BARRIER_NS = 2000000000ull;
 constexpr float TIE_REL = 1.0f / 16384.0f;      // 2^-14: Lloyd recheck band
 constexpr float CAND_REL = 1.0f / 4096.0f;      // 2^-12: farthest-point candidates
@@ -23,21 +24,10 @@ constexpr float MARGIN_REL = 1.0f / 4096.0f;    // 2^-12: rounding allowance of 
 constexpr double ROUND_UP = 1.0 + 1.0 / 1048576.0;
 
 // Phases recorded in the trace (one event per grid barrier passed by block 0).
-enum TracePhase { TR_ROOT = 1, TR_DIST1 = 2, TR_DIST2 = 3, TR_NODE = 4, TR_LLOYD = 5,
-                  TR_COUNT = 6, TR_SCATTER = 7, TR_CHILD = 8, TR_LPASS = 9, TR_LREPLAY = 10,
-                  TR_LUPDATE = 11, TR_LPUB = 12 };
-
-// Record a trace event from the group's block 0 outside a barrier.
-__device__ __forceinline__ void trace_event(long long* trace, int bid, int phase) {
-  if (bid == 0 && threadIdx.x == 0) {
-    const long long n = trace[0];
-    if (n < TRACE_CAP) {
-      trace[1 + 2 * n] = phase;
-      trace[2 + 2 * n] = (long long)globaltimer_ns();
-      trace[0] = n + 1;
-    }
-  }
-}
+// Events 9 and up are recorded by block 0 between barriers (its own progress).
+enum TracePhase { TR_ROOT = 1, TR_DIST1 = 2, TR_NODE = 4, TR_LLOYD = 5, TR_COUNT = 6,
+                  TR_SCATTER = 7, TR_CHILD = 8, TR_LPASS = 9, TR_LUPDATE = 11,
+                  TR_FWAIT = 12, TR_FSTAGE = 13, TR_FDONE = 14 };
 
 struct NodeRec {
   int start, count;   // segment of the permutation
@@ -53,6 +43,12 @@ struct SlotRec {      // a split in flight (block-local copy, identical in every
   int cnt_b_cur, cnt_b_acc;
   int split;          // produces children
   int recompute;      // centres to be recomputed from the assignment just made
+};
+
+struct SlotOut {      // a split after a Lloyd update, published by its finishing block
+  SlotRec r;
+  float slack, cabs;  // centre movement of the update; rounding allowance of the centres
+  double cum;         // total centre movement since the split started
 };
 
 struct ClArgs {
@@ -74,15 +70,22 @@ struct ClArgs {
   float* d32;         // N
   NodeRec* nodes;     // MAXNODES
   double* node_sum;   // MAXNODES x rho coordinate sums
-  float* pf;          // G x MAXSEG x (rho + 1) double-float pairs
+  float* pf;          // G x MAXSEG records of record_floats(rho) floats
   int* pi;            // G x MAXSEG x 2
   float* pd;          // G x MAXSEG
   double* pdd;        // G x MAXSEG
   int* px;            // G x MAXSEG
   int* chunk_cnt;     // max chunks
   long long* trace;   // [0] = count, then (phase, ns) pairs, block 0 only
-  double* fin;        // MAXACT x (rho + 2) reduced Lloyd sums, published by the owner blocks
+  unsigned* arrive;   // MAXACT arrival counters of the Lloyd partial sums (0 between passes)
+  SlotOut* sout;      // MAXACT splits after the last Lloyd update
+  double* gcen;       // MAXACT x 2 x rho centres after the last Lloyd update
+  double* gacc;       // MAXACT x rho accepted side-b coordinate sums
 };
+
+// Floats per partial record of a block: rho double-float pairs and one more
+// pair, padded to 16 bytes (records are fetched by bulk copies).
+__host__ __device__ constexpr int record_floats(int rho) { return ((2 * (rho + 1) + 3) / 4) * 4; }
 
 // Host helpers (k_cluster.cu).
 int grid_blocks(int dev);

@@ -66,6 +66,8 @@ struct ClShared {
   int redx[CL_WARPS];
   int scanw[CL_WARPS];
   int hlist[CH];          // positions of a chunk that need the full test
+  int wtab[PPT * CL_WARPS];   // per (u, warp) counts, then their exclusive prefix
+  int wtotal;
   float segmax[MAXSEG];
   float slack[MAXACT];   // centre movement of the last update
   double cum[MAXACT];    // total centre movement since the split started
@@ -74,47 +76,104 @@ struct ClShared {
   int segarg[MAXSEG];
   int ok;
   int all_done;
+  int tr_n;              // trace events recorded (block 0)
+  unsigned long long mbar;   // completion barrier of the record bulk copies
+  unsigned mb_phase;         // its current phase parity
+  float bmax;            // block maximum of the last block_max_sum
+  int last;              // this block is the last contributor of a split
 };
 
 __device__ __forceinline__ bool better(double d1, int i1, double d2, int i2) {
   return d1 > d2 || (d1 == d2 && i1 < i2);
 }
 
-// Grid barrier with a bounded wait.  Returns false if the device status
-// records an error (this block or another gave up), in which case the
-// caller returns.
+// Trace event of the group's block 0 (thread 0): the event count lives in
+// shared memory, so recording is two stores and no global round trip.
+__device__ __forceinline__ void trace_event(long long* trace, int bid, int& count, int phase) {
+  if (bid == 0 && threadIdx.x == 0 && count < TRACE_CAP) {
+    trace[1 + 2 * count] = phase;
+    trace[2 + 2 * count] = (long long)globaltimer_ns();
+    ++count;
+    trace[0] = count;
+  }
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Bulk copy (async proxy) global -> shared, completion counted in bytes on
+// an mbarrier.  Addresses and size multiples of 16 bytes.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes,
+                                              unsigned long long* mbar) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const unsigned m = (unsigned)__cvta_generic_to_shared(mbar);
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(d), "l"(src), "r"(bytes), "r"(m) : "memory");
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* mbar, unsigned count) {
+  const unsigned m = (unsigned)__cvta_generic_to_shared(mbar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(m), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* mbar, unsigned bytes) {
+  const unsigned m = (unsigned)__cvta_generic_to_shared(mbar);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(m), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async;" ::: "memory");
+}
+// Wait for the phase of the given parity to complete; false after limit_ns.
+__device__ __forceinline__ int mbar_wait(unsigned long long* mbar, unsigned parity,
+                                         unsigned long long limit_ns) {
+  const unsigned m = (unsigned)__cvta_generic_to_shared(mbar);
+  const unsigned long long t0 = globaltimer_ns();
+  while (true) {
+    unsigned done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(m), "r"(parity) : "memory");
+    if (done) return 1;
+    if (globaltimer_ns() - t0 > limit_ns) return 0;
+  }
+}
+
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid barrier with a bounded wait.  One monotonically growing arrival
+// counter per launch: the gen-th barrier is passed once it reaches gen * G,
+// so a block arrives with a single atomic and nobody resets anything.  The
+// wait gives up after BARRIER_NS (recording HDF_ETIMEOUT), or as soon as the
+// device status records an error from another block.  Returns false if the
+// device status records an error, in which case the caller returns.
 __device__ bool grid_barrier(const ClArgs& a, unsigned& gen, ClShared& s, int phase) {
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned* cnt = (unsigned*)(a.ctrl + CTRL_BARRIER);
-    volatile unsigned* vgen = (volatile unsigned*)(a.ctrl + CTRL_BARRIER_GEN);
+    ++gen;
+    const unsigned target = gen * (unsigned)a.G;
     __threadfence();
-    const unsigned arrived = atomicAdd(cnt, 1u);
-    if (arrived == (unsigned)a.G - 1) {
-      atomicExch(cnt, 0u);
-      __threadfence();
-      atomicAdd((unsigned*)(a.ctrl + CTRL_BARRIER_GEN), 1u);
-    } else {
+    const unsigned arrived = atomicAdd(cnt, 1u) + 1u;
+    if (arrived < target) {
       const unsigned long long t0 = globaltimer_ns();
-      while (*vgen == gen) {
-        __nanosleep(32);
-        if (globaltimer_ns() - t0 > BARRIER_NS) {
-          record_error(a.ctrl, HDF_ETIMEOUT);
-          break;
+      unsigned k = 0;
+      while (ld_acquire_gpu(cnt) < target) {
+        if ((++k & 31u) == 0) {
+          if (*(volatile int*)(a.ctrl + CTRL_ERROR) != 0) break;
+          if (globaltimer_ns() - t0 > BARRIER_NS) {
+            record_error(a.ctrl, HDF_ETIMEOUT);
+            break;
+          }
         }
       }
     }
     __threadfence();
-    ++gen;
     s.ok = (*(volatile int*)(a.ctrl + CTRL_ERROR) == 0);
-    if (a.bid == 0) {
-      const long long n = a.trace[0];
-      if (n < TRACE_CAP) {
-        a.trace[1 + 2 * n] = phase;
-        a.trace[2 + 2 * n] = (long long)globaltimer_ns();
-        a.trace[0] = n + 1;
-      }
-    }
+    trace_event(a.trace, a.bid, s.tr_n, phase);
   }
   __syncthreads();
   return s.ok != 0;
@@ -194,6 +253,15 @@ __device__ __forceinline__ double quotient(double x, double y) {
   double q = x * r;
   const double e = fma(-q, y, x);
   return fma(e, r, q);
+}
+
+// An upper bound of sqrt(x), x >= 0: FP32 square root (the FP64 one is slow
+// on this GPU) of the rounded value, scaled up by 2^-20 relative, which covers
+// the < 2^-23 relative error of the conversion and of sqrtf; FP64 where the
+// FP32 value would be subnormal.
+__device__ __forceinline__ double sqrt_up(double x) {
+  if (!(x >= 1e-36 && x <= 1e36)) return sqrt(x);
+  return (double)sqrtf((float)x) * ROUND_UP;
 }
 
 // Deterministic replay of a cross-block reduction, run identically by every
@@ -381,6 +449,43 @@ __device__ int block_excl_scan(int v, ClShared& s, int* total) {
   return before + x - v;
 }
 
+// Ranks in position order of the flagged points of a chunk whose positions
+// are base + u * CL_THREADS + tid (u < PPT): rank[u] = number of flagged
+// points at smaller positions (valid where flag[u]); returns the total.  The
+// per-(u, warp) ballot counts are prefixed over the 64 (u, warp) pairs in
+// position order by warp 0.  Three block barriers.
+__device__ int position_ranks(const bool (&flag)[PPT], int (&rank)[PPT], ClShared& s) {
+  static_assert(PPT * CL_WARPS == 64, "the prefix runs over 64 (u, warp) counts");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int pre[PPT];
+#pragma unroll
+  for (int u = 0; u < PPT; ++u) {
+    const unsigned bal = __ballot_sync(0xffffffffu, flag[u]);
+    pre[u] = __popc(bal & ((1u << lane) - 1u));
+    if (lane == 0) s.wtab[u * CL_WARPS + warp] = __popc(bal);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int v0 = s.wtab[2 * lane], v1 = s.wtab[2 * lane + 1];
+    int x = v0 + v1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    const int ex = x - v0 - v1;
+    s.wtab[2 * lane] = ex;
+    s.wtab[2 * lane + 1] = ex + v0;
+    if (lane == 31) s.wtotal = x;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < PPT; ++u) rank[u] = s.wtab[u * CL_WARPS + warp] + pre[u];
+  const int total = s.wtotal;
+  __syncthreads();   // wtab / wtotal may be rewritten by the next call
+  return total;
+}
+
 // Block max of a float and sum of a float; results written by thread 0.
 __device__ void block_max_sum(float m, F2 sum, ClShared& s, float* out_max, float* out_sum) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -404,6 +509,7 @@ __device__ void block_max_sum(float m, F2 sum, ClShared& s, float* out_max, floa
       ss = f2_add(ss, u);
     }
     *out_max = mm;
+    s.bmax = mm;
     out_sum[0] = ss.hi;
     out_sum[1] = ss.lo;
   }
@@ -432,8 +538,8 @@ __device__ void block_argmax(double d, int idx, ClShared& s, double* out_d, int*
 }
 
 // Coordinate d of the point at permutation position pos.
-__device__ __forceinline__ float xat(const ClArgs& a, int d, int pos) {
-  return __ldcg(a.X + (size_t)d * a.N + pos);
+__device__ __forceinline__ float xat(const float* X, size_t N, int d, int pos) {
+  return __ldcg(X + (size_t)d * N + pos);
 }
 
 // Replay of the sequential greedy rule on the known tree (warp 0).  Leaves
@@ -493,16 +599,23 @@ __host__ __device__ constexpr size_t dyn_c64_offset(int rho) {
   return ((sizeof(float) * MAXSEG * (size_t)rho + 15) / 16) * 16;
 }
 
-__host__ __device__ constexpr size_t dyn_smem_bytes(int rho) {
+__host__ __device__ constexpr size_t dyn_red_offset(int rho) {
   return dyn_c64_offset(rho) + sizeof(double) * ((size_t)MAXSEG * rho + (size_t)MAXACT * (rho + 2) +
                                                  3 * (size_t)MAXACT * rho);
+}
+
+// ... plus the staging area of one split's partial records (MAXG records)
+// and the per-class partial sums of their reduction (CL_THREADS pairs).
+__host__ __device__ constexpr size_t dyn_smem_bytes(int rho) {
+  return ((dyn_red_offset(rho) + 127) / 128) * 128 +
+         sizeof(float) * ((size_t)MAXG * record_floats(rho) + 2 * CL_THREADS);
 }
 
 // The clustering of one guide by the blocks of its group.
 template <int RMAX>
 __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
   const int rho = a.rho;
-  const int PS = 2 * (rho + 1);   // floats per partial record (pairs)
+  const int PS = record_floats(rho);   // floats per partial record (pairs, padded)
   float* c32 = (float*)dyn;                                   // MAXSEG x rho
   double* c64 = (double*)(dyn + dyn_c64_offset(rho));         // MAXSEG x rho
   double* tmp = c64 + MAXSEG * rho;                           // MAXACT x (rho + 2)
@@ -510,15 +623,28 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
   double* nsum = acc_sum + MAXACT * rho;                      // MAXACT x rho sums of the split nodes
   double* mean_a = nsum + MAXACT * rho;                       // MAXACT x rho
   auto acc_sum_a = [&](int i, int d) -> double& { return mean_a[i * rho + d]; };
+  float* red = (float*)(dyn + ((dyn_red_offset(rho) + 127) / 128) * 128);   // MAXG records
+  float* parts = red + (size_t)MAXG * PS;                                    // CL_THREADS pairs
   unsigned gen = 0;
   const int tid = threadIdx.x, bid = a.bid;
   const size_t N = (size_t)a.N;
+  // Points in permutation order (X, raster indices P) and the scatter
+  // targets of the partition (Xn, Pn).  Only the split segments are moved,
+  // so the children's points are copied back into X / P by the next
+  // distance pass (the other leaves never leave X).
+  float* const X = a.X;
+  float* const Xn = a.X2;
+  uint32_t* const P = a.perm;
+  uint32_t* const Pn = a.perm2;
   int nnodes = 1, rounds = 0, lloyd_max = 0;
   // points whose coordinates are loaded together (registers permitting)
   constexpr int UB = RMAX <= 4 ? 8 : (RMAX <= 8 ? 4 : (RMAX <= 32 ? 2 : 1));
   static_assert(PPT % UB == 0, "load batch must divide the points per thread");
+  static_assert(PPT * CL_WARPS == 64, "the partition's prefix runs over 64 (u, warp) counts");
 
   // ------------------------------------------------------------ root node
+  if (bid == 0 && tid < MAXACT) a.arrive[tid] = 0u;   // ordered before any use by the root barrier
+  if (tid == 0) s.tr_n = 0;
   if (tid == 0) {
     s.nseg = 1;
     s.seg_start[0] = 0;
@@ -547,11 +673,11 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
             for (int b = 0; b < UB; ++b) {
               const int pos = base + (u0 + b) * CL_THREADS + tid;
               if (pos >= end) continue;
-              a.perm[pos] = (uint32_t)pos;
+              P[pos] = (uint32_t)pos;
 #pragma unroll
               for (int d = 0; d < RMAX; ++d) {
                 if (d < rho) {
-                  a.X[(size_t)d * N + pos] = x[b][d];
+                  X[(size_t)d * N + pos] = x[b][d];
                   two_sum_acc(hi[d], lo[d], x[b][d]);
                 }
               }
@@ -582,26 +708,33 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
 
   // Distance statistics of every segment of the table against the centres
   // c32[seg] / c64[seg]: SSE, then the farthest point decided in FP64 among
-  // the FP32 candidates (ties -> lowest raster index).  `from_scratch` reads
-  // the points (and raster indices) from the scatter buffers and moves them
-  // into place.  Results in s.segmax / s.segsse / s.segarg.  Two barriers.
+  // the FP32 candidates (ties -> lowest raster index).  Results in s.segmax /
+  // s.segsse / s.segarg.  `from_scratch` reads the points (and raster
+  // indices) from the scatter buffers and moves them into place.  One grid
+  // barrier: each block takes its own FP64
+  // candidates relative to its own FP32 maximum; the global FP64 maximiser
+  // lies within 2^-12 of the global FP32 maximum, hence of its block's
+  // maximum, so it is its block's winner and the replay of the block winners
+  // returns it.
   auto dist_stats = [&](bool from_scratch) -> bool {
     {
       float mx = -1.0f;
       F2 sse{0.0f, 0.0f};
+      int seg_first_chunk = -1;
       for_blocks(a, s,
-          [&](int seg, int base, int end, int) {
+          [&](int seg, int base, int end, int j) {
+            if (seg_first_chunk < 0) seg_first_chunk = j;
             const float* c = c32 + seg * rho;
 #pragma unroll
             for (int u0 = 0; u0 < PPT; u0 += UB) {
               float x[UB][RMAX];
               uint32_t pid[UB];
+              const float* src = from_scratch ? Xn : X;
 #pragma unroll
               for (int b = 0; b < UB; ++b) {
                 const int pos = base + (u0 + b) * CL_THREADS + tid;
                 const bool v = pos < end;
-                const float* src = from_scratch ? a.X2 : a.X;
-                pid[b] = (v && from_scratch) ? __ldcg(a.perm2 + pos) : 0u;
+                pid[b] = (v && from_scratch) ? __ldcg(Pn + pos) : 0u;
 #pragma unroll
                 for (int d = 0; d < RMAX; ++d)
                   x[b][d] = (v && d < rho) ? __ldcg(src + (size_t)d * N + pos) : 0.0f;
@@ -614,12 +747,12 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
 #pragma unroll
                 for (int d = 0; d < RMAX; ++d) {
                   if (d < rho) {
-                    if (from_scratch) a.X[(size_t)d * N + pos] = x[b][d];
+                    if (from_scratch) X[(size_t)d * N + pos] = x[b][d];
                     const float t = x[b][d] - c[d];
                     d2 = fmaf(t, t, d2);
                   }
                 }
-                if (from_scratch) a.perm[pos] = pid[b];
+                if (from_scratch) P[pos] = pid[b];
                 a.d32[pos] = d2;
                 mx = fmaxf(mx, d2);
                 two_sum_acc(sse.hi, sse.lo, d2);
@@ -627,10 +760,48 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
             }
           },
           [&](int seg) {
-            block_max_sum(mx, sse, s, a.pd + (size_t)bid * MAXSEG + seg,
-                          a.pf + ((size_t)bid * MAXSEG + seg) * PS);
+            const size_t off = (size_t)bid * MAXSEG + seg;
+            block_max_sum(mx, sse, s, a.pd + off, a.pf + off * PS);   // ends with a block sync
+            const float m = s.bmax;                                   // this block's maximum
+            // FP64 candidates of this block's chunks of the segment
+            double bd = -1.0;
+            int bi = 0x7fffffff;
+            for (int j = seg_first_chunk; j < s.seg_chunk0[seg + 1]; j += a.G) {
+              const int base = s.seg_start[seg] + (j - s.seg_chunk0[seg]) * CH;
+              const int end = s.seg_start[seg] + s.seg_count[seg];
+              float dd[PPT];
+#pragma unroll
+              for (int u = 0; u < PPT; ++u) {
+                const int pos = base + u * CL_THREADS + tid;
+                dd[u] = (pos < end) ? __ldcg(a.d32 + pos) : -1.0f;
+              }
+#pragma unroll
+              for (int u = 0; u < PPT; ++u) {
+                const int pos = base + u * CL_THREADS + tid;
+                if (pos >= end) continue;
+                if (m > 0.0f && dd[u] < m * (1.0f - CAND_REL)) continue;
+                const int idx = (int)__ldcg(P + pos);
+                double e = 0.0;
+                if (m > 0.0f) {
+                  const double* cc = c64 + (size_t)seg * rho;
+                  float xv[RMAX];
+#pragma unroll
+                  for (int d = 0; d < RMAX; ++d) xv[d] = (d < rho) ? xat(X, N, d, pos) : 0.0f;
+#pragma unroll
+                  for (int d = 0; d < RMAX; ++d) {
+                    if (d < rho) {
+                      const double t = (double)xv[d] - cc[d];
+                      e = fma(t, t, e);
+                    }
+                  }
+                }
+                if (better(e, idx, bd, bi)) { bd = e; bi = idx; }
+              }
+            }
+            block_argmax(bd, bi, s, a.pdd + off, a.px + off);
             mx = -1.0f;
             sse = F2{0.0f, 0.0f};
+            seg_first_chunk = -1;
           });
     }
     if (!grid_barrier(a, gen, s, TR_DIST1)) return false;
@@ -645,61 +816,14 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
             return F2{__ldcg(q), __ldcg(q + 1)};
           },
           [](F2 x, F2 y) { return f2_add(x, y); }, [&](int seg, F2 t) { s.segsse[seg] = f2_to_d(t); });
-    }
-    __syncthreads();
-    {
-      double bd = -1.0;
-      int bi = 0x7fffffff;
-      for_blocks(a, s,
-          [&](int seg, int base, int end, int) {
-            const float m = s.segmax[seg];
-            float dd[PPT];
-#pragma unroll
-            for (int u = 0; u < PPT; ++u) {
-              const int pos = base + u * CL_THREADS + tid;
-              dd[u] = (pos < end) ? __ldcg(a.d32 + pos) : -1.0f;
-            }
-#pragma unroll
-            for (int u = 0; u < PPT; ++u) {
-              const int pos = base + u * CL_THREADS + tid;
-              if (pos >= end) continue;
-              if (m > 0.0f && dd[u] < m * (1.0f - CAND_REL)) continue;
-              const int idx = (int)__ldcg(a.perm + pos);
-              double e = 0.0;
-              if (m > 0.0f) {
-                const double* c = c64 + (size_t)seg * rho;
-                float xv[RMAX];
-#pragma unroll
-                for (int d = 0; d < RMAX; ++d) xv[d] = (d < rho) ? xat(a, d, pos) : 0.0f;
-#pragma unroll
-                for (int d = 0; d < RMAX; ++d) {
-                  if (d < rho) {
-                    const double t = (double)xv[d] - c[d];
-                    e = fma(t, t, e);
-                  }
-                }
-              }
-              if (better(e, idx, bd, bi)) { bd = e; bi = idx; }
-            }
-          },
-          [&](int seg) {
-            block_argmax(bd, bi, s, a.pdd + (size_t)bid * MAXSEG + seg,
-                         a.px + (size_t)bid * MAXSEG + seg);
-            bd = -1.0;
-            bi = 0x7fffffff;
-          });
-    }
-    if (!grid_barrier(a, gen, s, TR_DIST2)) return false;
-    {
       ArgMax none;
       none.d = -1.0;
       none.i = 0x7fffffff;
-      replay<8>(s.nseg, none, [&](int seg) { return s.seg_on[seg] ? contrib_count(a, s, seg) : 0; },
+      replay<8>(s.nseg, none, ncf,
           [&](int seg, int i) {
-            const size_t off = (size_t)contrib_block(a, s, seg, i) * MAXSEG + seg;
             ArgMax r;
-            r.d = __ldcg(a.pdd + off);
-            r.i = __ldcg(a.px + off);
+            r.d = __ldcg(a.pdd + off(seg, i));
+            r.i = __ldcg(a.px + off(seg, i));
             return r;
           },
           [](ArgMax x, ArgMax y) { return better(y.d, y.i, x.d, x.i) ? y : x; },
@@ -815,6 +939,181 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
     __syncthreads();
     build_chunks(s);
 
+    // Arrival of this block's partial sums of split sl (written by the block
+    // before the barrier): one release-add, nobody waits for it.
+    auto arrive = [&](int sl) {
+      __syncthreads();
+      if (tid == 0) red_release_add(a.arrive + sl, 1u);
+    };
+    // The finishing block of split sl: one of the blocks with the fewest
+    // chunks (chunk j belongs to block j mod G), distinct for distinct splits.
+    auto finisher_of = [&](int sl) { return a.G - 1 - sl % a.G; };
+    // Wait (bounded) until every contributor of split sl has arrived.
+    auto wait_arrivals = [&](int sl) -> bool {
+      if (tid == 0) {
+        const unsigned need = (unsigned)contrib_count(a, s, sl);
+        int ok = 1;
+        if (ld_acquire_gpu(a.arrive + sl) < need) {
+          const unsigned long long t0 = globaltimer_ns();
+          unsigned k = 0;
+          while (ld_acquire_gpu(a.arrive + sl) < need) {
+            if ((++k & 31u) == 0) {
+              if (*(volatile int*)(a.ctrl + CTRL_ERROR) != 0) { ok = 0; break; }
+              if (globaltimer_ns() - t0 > BARRIER_NS) {
+                record_error(a.ctrl, HDF_ETIMEOUT);
+                ok = 0;
+                break;
+              }
+            }
+          }
+        }
+        a.arrive[sl] = 0u;   // the next arrivals come after the grid barrier
+        s.last = ok;
+      }
+      __syncthreads();
+      return s.last != 0;
+    };
+    // Bulk copies of the nc partial records of split i (record of contributor
+    // c at block contrib_block(c)) into dst, completed on the block's mbarrier;
+    // bounded wait.  False (device status set) if the copies did not land.
+    auto stage_records = [&](int i, int nc, float* dst) -> bool {
+      const unsigned bytes = (unsigned)(PS * sizeof(float));
+      if (tid == 0) {
+        fence_proxy_async();   // earlier generic accesses before the async writes
+        mbar_expect_tx(&s.mbar, bytes * (unsigned)nc);
+      }
+      __syncthreads();
+      for (int c = tid; c < nc; c += CL_THREADS) {
+        const size_t off = (size_t)contrib_block(a, s, i, c) * MAXSEG + i;
+        bulk_copy_g2s(dst + (size_t)c * PS, a.pf + off * PS, bytes, &s.mbar);
+      }
+      if (tid == 0) {
+        int ok = mbar_wait(&s.mbar, s.mb_phase, BARRIER_NS);
+        if (!ok) {
+          record_error(a.ctrl, HDF_ETIMEOUT);
+          mbar_wait(&s.mbar, s.mb_phase, BARRIER_NS);   // let the copies in flight land
+        }
+        s.mb_phase ^= 1u;
+        s.last = ok;
+      }
+      __syncthreads();
+      return s.last != 0;
+    };
+    // Lloyd update of split i by its finishing block: reduce the
+    // partial records in a fixed order (warp per value, lanes over the
+    // contributors, xor tree), decide the split's state, compute the new
+    // centres (means of the two sides) and the distance they moved, and
+    // publish all of it for the other blocks (read after the grid barrier).
+    auto finish_split = [&](int i, int it) -> bool {
+      const int nc = contrib_count(a, s, i);
+      const int V = rho + 2;
+      // Fetch the nc records into shared memory with bulk copies (all in
+      // flight at once), then reduce them in a fixed order: thread (g, v)
+      // sums value v of the records c = g, g + NG, ... (ascending), and
+      // fin[v] = ((part_0 + part_1) + ...) + part_{NG-1}.
+      if (!stage_records(i, nc, red)) return false;
+      const int VS = V <= 32 ? 32 : (V <= 64 ? 64 : 128);   // value slots
+      const int NG = CL_THREADS / VS;                        // record classes
+      {
+        const int v = tid % VS, g = tid / VS;
+        F2 t{0.0f, 0.0f};
+        if (v < V) {
+          for (int c = g; c < nc; c += NG) {
+            const float* r = red + (size_t)c * PS;
+            t = f2_add(t, v < rho ? F2{r[2 * v], r[2 * v + 1]}
+                                  : F2{(float)reinterpret_cast<const int*>(r)[2 * rho + (v - rho)], 0.0f});
+          }
+        }
+        reinterpret_cast<float2*>(parts)[g * VS + v] = make_float2(t.hi, t.lo);
+      }
+      __syncthreads();
+      trace_event(a.trace, a.bid, s.tr_n, TR_FSTAGE);
+      double* fin = tmp + i * (rho + 2);
+      for (int v = tid; v < V; v += CL_THREADS) {
+        F2 t{parts[2 * v], parts[2 * v + 1]};
+        for (int g = 1; g < NG; ++g) t = f2_add(t, F2{parts[2 * (g * VS + v)], parts[2 * (g * VS + v) + 1]});
+        fin[v] = f2_to_d(t);
+      }
+      __syncthreads();
+      // the update, by warp 0 alone (lanes over the coordinates)
+      if (tid < 32) {
+        const int lane = tid;
+        SlotRec& sl = s.slot[i];
+        int recompute = 0;
+        if (lane == 0) {
+          sl.recompute = 0;
+          const int cb = (it == 0 ? 0 : sl.cnt_b_acc) + (int)fin[rho];
+          const int changed = (int)fin[rho + 1];
+          if (it == 0 && (cb == 0 || cb == sl.count)) {          // degenerate pair: not splittable
+            sl.done = 1;
+            sl.split = 0;
+          } else if (it > 0 && (cb == 0 || cb == sl.count)) {    // a side would be empty:
+            sl.done = 1;                                          // keep the previous assignment
+            sl.rev_it = it;
+            sl.iters = it;
+          } else if (it > 0 && changed == 0) {                   // converged
+            sl.done = 1;
+            sl.iters = it;
+          } else {                                                // accept this assignment
+            sl.cnt_b_cur = cb;
+            sl.iters = it + 1;
+            sl.recompute = 1;
+            if (it + 1 == MAX_LLOYD) sl.done = 1;
+          }
+          recompute = sl.recompute;
+        }
+        __syncwarp();
+        recompute = __shfl_sync(0xffffffffu, recompute, 0);
+        if (recompute) {
+          // accepted sums, the new means (a, b) and the distance each centre moved
+          const double nb_cnt = (double)sl.cnt_b_cur, na_cnt = (double)(sl.count - sl.cnt_b_cur);
+          double ma2 = 0.0, mb2 = 0.0, na = 0.0, nb = 0.0;
+          for (int d = lane; d < rho; d += 32) {
+            const double sb = fin[d] + (it > 0 ? acc_sum[i * rho + d] : 0.0);
+            acc_sum[i * rho + d] = sb;
+            const double mb = quotient(sb, nb_cnt);
+            const double ma = quotient(nsum[i * rho + d] - sb, na_cnt);
+            const double ua = ma - c64[(2 * i) * rho + d], ub = mb - c64[(2 * i + 1) * rho + d];
+            ma2 += ua * ua;
+            mb2 += ub * ub;
+            na += ma * ma;
+            nb += mb * mb;
+            c64[(2 * i) * rho + d] = ma;
+            c64[(2 * i + 1) * rho + d] = mb;
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            ma2 += __shfl_xor_sync(0xffffffffu, ma2, o);
+            mb2 += __shfl_xor_sync(0xffffffffu, mb2, o);
+            na += __shfl_xor_sync(0xffffffffu, na, o);
+            nb += __shfl_xor_sync(0xffffffffu, nb, o);
+          }
+          if (lane == 0) {
+            s.slack[i] = (float)((sqrt_up(ma2) + sqrt_up(mb2)) * ROUND_UP) + 1e-30f;
+            s.cum[i] = (s.cum[i] + (double)s.slack[i]) * ROUND_UP;
+            s.cabs[i] = (float)((sqrt_up(na) + sqrt_up(nb)) * (1.0 / 1048576.0));
+            sl.cnt_b_acc = sl.cnt_b_cur;
+          }
+        }
+        __syncwarp();
+        // publish
+        for (int v = lane; v < 3 * rho; v += 32) {
+          if (v < 2 * rho) a.gcen[(size_t)i * 2 * rho + v] = c64[2 * i * rho + v];
+          else a.gacc[(size_t)i * rho + v - 2 * rho] = acc_sum[i * rho + v - 2 * rho];
+        }
+        if (lane == 0) {
+          SlotOut o;
+          o.r = sl;
+          o.slack = s.slack[i];
+          o.cabs = s.cabs[i];
+          o.cum = s.cum[i];
+          a.sout[i] = o;
+        }
+      }
+      __syncthreads();
+      return true;
+    };
+
     // ---- Lloyd iterations, all splits of the round together
     for (int it = 0; it < MAX_LLOYD; ++it) {
       const int all_done = __syncthreads_and(tid < s.nslots ? s.slot[tid].done : 1);
@@ -838,15 +1137,13 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
                 const float m0 = (pos < end && it > 0) ? __ldcg(a.marg + pos) : -1.0f;
                 heavy[u] = pos < end && !(m0 - cum > 1e-6f * (fabsf(m0) + cum));
               }
-              // compact the chunk's heavy points and spread them over the block
-              int nh = 0;
-#pragma unroll
-              for (int u = 0; u < PPT; ++u) nh += heavy[u];
-              int nheavy;
-              int k = block_excl_scan(nh, s, &nheavy);
+              // compact the chunk's heavy points in position order (coalesced
+              // loads where they are dense) and spread them over the block
+              int hr[PPT];
+              const int nheavy = position_ranks(heavy, hr, s);
 #pragma unroll
               for (int u = 0; u < PPT; ++u)
-                if (heavy[u]) s.hlist[k++] = base + u * CL_THREADS + tid;
+                if (heavy[u]) s.hlist[hr[u]] = base + u * CL_THREADS + tid;
               __syncthreads();
               const float* ca = c32 + (2 * seg) * rho;
               const float* cb = ca + rho;
@@ -859,7 +1156,7 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
                   hp[b] = q < nheavy ? s.hlist[q] : -1;
 #pragma unroll
                   for (int d = 0; d < RMAX; ++d)
-                    x[b][d] = (hp[b] >= 0 && d < rho) ? xat(a, d, hp[b]) : 0.0f;
+                    x[b][d] = (hp[b] >= 0 && d < rho) ? xat(X, N, d, hp[b]) : 0.0f;
                 }
 #pragma unroll
                 for (int b = 0; b < UB; ++b) {
@@ -917,133 +1214,54 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
             [&](int seg) {
               const size_t off = (size_t)bid * MAXSEG + seg;
               block_sum_f2<RMAX>(hi, lo, rho, s, a.pf + off * PS);
-              block_sum_i2(cnt, chg, s, a.pi + off * 2);
+              block_sum_i2(cnt, chg, s, reinterpret_cast<int*>(a.pf + off * PS + 2 * rho));
 #pragma unroll
               for (int d = 0; d < RMAX; ++d) hi[d] = lo[d] = 0.0f;
               cnt = 0;
               chg = 0;
+              arrive(seg);
             });
       }
-      trace_event(a.trace, a.bid, TR_LPASS);
+      // finish the splits this block is the finishing block of
+      for (int sl = 0; sl < s.nslots; ++sl) {
+        if (!s.seg_on[sl] || finisher_of(sl) != bid) continue;
+        if (!wait_arrivals(sl)) return;
+        trace_event(a.trace, a.bid, s.tr_n, TR_FWAIT);
+        if (!finish_split(sl, it)) return;
+        trace_event(a.trace, a.bid, s.tr_n, TR_FDONE);
+      }
+      trace_event(a.trace, a.bid, s.tr_n, TR_LPASS);
       if (!grid_barrier(a, gen, s, TR_LLOYD)) return;
-      // replay the reduction of every active split: side-b sums, count, changes
-      // Each split's partial sums are reduced by its owner block (split i ->
-      // block i mod G) in a fixed order and published; one more barrier, then
-      // every block reads the published values.
-      for (int sl = bid; sl < s.nslots; sl += a.G) {
-        if (s.slot[sl].done) continue;
-        const int nc = contrib_count(a, s, sl);
-        const int lane = tid & 31, warp = tid >> 5;
-        for (int d0 = warp; d0 < rho + 2; d0 += CL_WARPS) {
-          F2 t{0.0f, 0.0f};
-          for (int i = lane; i < nc; i += 32) {
-            const size_t off = (size_t)contrib_block(a, s, sl, i) * MAXSEG + sl;
-            const F2 v = d0 < rho ? F2{__ldcg(a.pf + off * PS + 2 * d0), __ldcg(a.pf + off * PS + 2 * d0 + 1)}
-                                  : F2{(float)__ldcg(a.pi + off * 2 + (d0 - rho)), 0.0f};
-            t = f2_add(t, v);
-          }
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) t = f2_add(t, shfl_xor_t(t, o));
-          if (lane == 0) a.fin[sl * (rho + 2) + d0] = f2_to_d(t);
-        }
+      // every block takes the published state of the splits that were active
+      for (int v = tid; v < s.nslots * 3 * rho; v += CL_THREADS) {
+        const int i = v / (3 * rho), r = v % (3 * rho);
+        if (!s.seg_on[i]) continue;
+        if (r < 2 * rho) c64[2 * i * rho + r] = __ldcg(a.gcen + (size_t)i * 2 * rho + r);
+        else acc_sum[i * rho + r - 2 * rho] = __ldcg(a.gacc + (size_t)i * rho + r - 2 * rho);
       }
-      if (!grid_barrier(a, gen, s, TR_LPUB)) return;
-      for (int v = tid; v < s.nslots * (rho + 2); v += CL_THREADS)
-        tmp[v] = s.slot[v / (rho + 2)].done ? 0.0 : __ldcg(a.fin + v);
-      __syncthreads();
-      trace_event(a.trace, a.bid, TR_LREPLAY);
       for (int i = tid; i < s.nslots; i += CL_THREADS) {
-        {
-          SlotRec& sl = s.slot[i];
-          sl.recompute = 0;
-          if (sl.done) continue;
-          const int cb = (it == 0 ? 0 : sl.cnt_b_acc) + (int)tmp[i * (rho + 2) + rho];
-          const int changed = (int)tmp[i * (rho + 2) + rho + 1];
-          if (it == 0 && (cb == 0 || cb == sl.count)) {   // degenerate pair: not splittable
-            sl.done = 1;
-            sl.split = 0;
-            continue;
-          }
-          if (it > 0 && (cb == 0 || cb == sl.count)) {   // a side would be empty:
-            sl.done = 1;                                    // keep the previous assignment
-            sl.rev_it = it;
-            sl.iters = it;
-            continue;
-          }
-          if (it > 0 && changed == 0) {                    // converged
-            sl.done = 1;
-            sl.iters = it;
-            continue;
-          }
-                                                            // accept this assignment
-          sl.cnt_b_cur = cb;
-          sl.iters = it + 1;
-          sl.recompute = 1;
-          if (it + 1 == MAX_LLOYD) sl.done = 1;
-        }
+        if (!s.seg_on[i]) continue;
+        const SlotOut* o = a.sout + i;
+        SlotRec& sl = s.slot[i];
+        sl.done = __ldcg(&o->r.done);
+        sl.iters = __ldcg(&o->r.iters);
+        sl.rev_it = __ldcg(&o->r.rev_it);
+        sl.cnt_b_cur = __ldcg(&o->r.cnt_b_cur);
+        sl.cnt_b_acc = __ldcg(&o->r.cnt_b_acc);
+        sl.split = __ldcg(&o->r.split);
+        sl.recompute = __ldcg(&o->r.recompute);
+        s.slack[i] = __ldcg(&o->slack);
+        s.cabs[i] = __ldcg(&o->cabs);
+        s.cum[i] = __ldcg(&o->cum);
       }
       __syncthreads();
-      // accepted sums and the new centres (means of the two sides); the distance
-      // each centre moved bounds the change of every stored margin
-      for (int v = tid; v < s.nslots * rho; v += CL_THREADS) {
-        const int i = v / rho, d = v % rho;
-        if (s.slot[i].recompute && it > 0) tmp[i * (rho + 2) + d] += acc_sum[i * rho + d];
-      }
+      for (int v = tid; v < s.nslots * 2 * rho; v += CL_THREADS)
+        if (s.seg_on[v / (2 * rho)]) c32[v] = (float)c64[v];
       __syncthreads();
-      // new means (stored in tmp) and the distance each centre moved
-      for (int v = tid; v < s.nslots * rho; v += CL_THREADS) {
-        const int i = v / rho, d = v % rho;
-        const SlotRec& sl = s.slot[i];
-        if (!sl.recompute) continue;
-        const double sb = tmp[i * (rho + 2) + d];
-        acc_sum[i * rho + d] = sb;
-        tmp[i * (rho + 2) + d] = quotient(sb, (double)sl.cnt_b_cur);                        // mean b
-        acc_sum_a(i, d) = quotient(nsum[i * rho + d] - sb, (double)(sl.count - sl.cnt_b_cur));  // mean a
-      }
-      __syncthreads();
-      for (int i = tid >> 5; i < s.nslots; i += CL_WARPS) {
-        const SlotRec& sl = s.slot[i];
-        if (!sl.recompute) continue;
-        double ma2 = 0.0, mb2 = 0.0, na = 0.0, nb = 0.0;
-        for (int d = tid & 31; d < rho; d += 32) {
-          const double ma = acc_sum_a(i, d), mb = tmp[i * (rho + 2) + d];
-          const double ua = ma - c64[(2 * i) * rho + d], ub = mb - c64[(2 * i + 1) * rho + d];
-          ma2 += ua * ua;
-          mb2 += ub * ub;
-          na += ma * ma;
-          nb += mb * mb;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          ma2 += __shfl_xor_sync(0xffffffffu, ma2, o);
-          mb2 += __shfl_xor_sync(0xffffffffu, mb2, o);
-          na += __shfl_xor_sync(0xffffffffu, na, o);
-          nb += __shfl_xor_sync(0xffffffffu, nb, o);
-        }
-        if ((tid & 31) == 0) {
-          s.slack[i] = (float)((sqrt(ma2) + sqrt(mb2)) * ROUND_UP) + 1e-30f;
-          s.cum[i] = (s.cum[i] + (double)s.slack[i]) * ROUND_UP;
-          s.cabs[i] = (float)((sqrt(na) + sqrt(nb)) * (1.0 / 1048576.0));
-        }
-      }
-      __syncthreads();
-      for (int v = tid; v < s.nslots * rho; v += CL_THREADS) {
-        const int i = v / rho, d = v % rho;
-        if (!s.slot[i].recompute) continue;
-        const double ma = acc_sum_a(i, d), mb = tmp[i * (rho + 2) + d];
-        c64[(2 * i) * rho + d] = ma;
-        c64[(2 * i + 1) * rho + d] = mb;
-        c32[(2 * i) * rho + d] = (float)ma;
-        c32[(2 * i + 1) * rho + d] = (float)mb;
-      }
-      __syncthreads();
-      for (int i = tid; i < s.nslots; i += CL_THREADS) {
-        if (s.slot[i].recompute) s.slot[i].cnt_b_acc = s.slot[i].cnt_b_cur;
-        s.seg_on[i] = !s.slot[i].done;
-      }
+      if (tid < s.nslots) s.seg_on[tid] = !s.slot[tid].done;
       __syncthreads();
       build_chunks(s);
-      trace_event(a.trace, a.bid, TR_LUPDATE);
+      trace_event(a.trace, a.bid, s.tr_n, TR_LUPDATE);
     }
     if (tid == 0) {
       for (int i = 0; i < s.nslots; ++i) {
@@ -1055,8 +1273,10 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
     build_chunks(s);
 
     // ---- stable partition of every split segment: side-a points first.
-    // Within a chunk thread t owns the PPT consecutive positions
-    // base + t*PPT + u, so one block-wide scan per chunk ranks the points.
+    // A chunk's positions are base + u * CL_THREADS + tid (u < PPT), so the
+    // loads are coalesced; a point's rank among the chunk's side-b points is
+    // the prefix over (u, warp) of the warps' ballot counts plus its rank in
+    // its warp's ballot.
     auto chunk_geom = [&](int j, int& seg, int& base, int& end) {
       while (s.seg_chunk0[seg + 1] <= j) ++seg;
       base = s.seg_start[seg] + (j - s.seg_chunk0[seg]) * CH;
@@ -1092,7 +1312,7 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
         int c = 0;
 #pragma unroll
         for (int u = 0; u < PPT; ++u) {
-          const int pos = base + tid * PPT + u;
+          const int pos = base + u * CL_THREADS + tid;
           if (pos < end) c += accepted_side(a, pos, rv);
         }
         int total;
@@ -1113,23 +1333,23 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
         for (int q = s.seg_chunk0[seg] + tid; q < j; q += CL_THREADS) pb += __ldcg(a.chunk_cnt + q);
         int before_b_chunk;
         block_scan(pb, before_b_chunk);
-        int sdv[PPT], c = 0;
+        bool sdv[PPT];
+        int rk[PPT];
 #pragma unroll
         for (int u = 0; u < PPT; ++u) {
-          const int pos = base + tid * PPT + u;
-          sdv[u] = (pos < end) ? accepted_side(a, pos, rv) : 0;
-          c += sdv[u];
+          const int pos = base + u * CL_THREADS + tid;
+          sdv[u] = (pos < end) && accepted_side(a, pos, rv) != 0;
         }
-        int total;
-        int rank_b = before_b_chunk + block_scan(c, total);
+        position_ranks(sdv, rk, s);
         const int cnt_a = sl.count - sl.cnt_b_acc;
         int np[PPT];
 #pragma unroll
         for (int u = 0; u < PPT; ++u) {
-          const int pos = base + tid * PPT + u;
+          const int pos = base + u * CL_THREADS + tid;
           np[u] = -1;
           if (pos >= end) continue;
-          if (sdv[u]) np[u] = sl.start + cnt_a + rank_b++;
+          const int rank_b = before_b_chunk + rk[u];   // side-b points before pos (valid for either side)
+          if (sdv[u]) np[u] = sl.start + cnt_a + rank_b;
           else np[u] = sl.start + (pos - sl.start - rank_b);   // side-a points before = offset - side-b before
           if (np[u] < sl.start || np[u] >= sl.start + sl.count) {
             record_error(a.ctrl, HDF_EDOMAIN);   // inconsistent counts: never write outside
@@ -1142,20 +1362,20 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
           uint32_t pid[UB];
 #pragma unroll
           for (int b = 0; b < UB; ++b) {
-            const int pos = base + tid * PPT + u0 + b;
+            const int pos = base + (u0 + b) * CL_THREADS + tid;
             const bool v = np[u0 + b] >= 0;
-            pid[b] = v ? __ldcg(a.perm + pos) : 0u;
+            pid[b] = v ? __ldcg(P + pos) : 0u;
 #pragma unroll
-            for (int d = 0; d < RMAX; ++d) x[b][d] = (v && d < rho) ? xat(a, d, pos) : 0.0f;
+            for (int d = 0; d < RMAX; ++d) x[b][d] = (v && d < rho) ? xat(X, N, d, pos) : 0.0f;
           }
 #pragma unroll
           for (int b = 0; b < UB; ++b) {
             const int q = np[u0 + b];
             if (q < 0) continue;
-            a.perm2[q] = pid[b];
+            Pn[q] = pid[b];
 #pragma unroll
             for (int d = 0; d < RMAX; ++d)
-              if (d < rho) a.X2[(size_t)d * N + q] = x[b][d];
+              if (d < rho) Xn[(size_t)d * N + q] = x[b][d];
           }
         }
       }
@@ -1252,7 +1472,7 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
 #pragma unroll
         for (int u = 0; u < PPT; ++u) {
           const int pos = base + u * CL_THREADS + tid;
-          idx[u] = (pos < end) ? __ldcg(a.perm + pos) : 0xffffffffu;
+          idx[u] = (pos < end) ? __ldcg(P + pos) : 0xffffffffu;
         }
 #pragma unroll
         for (int u = 0; u < PPT; ++u)
@@ -1275,8 +1495,10 @@ cluster_kernel(const ClArgs* __restrict__ table, const int4* __restrict__ groups
   __shared__ ClShared s;
   __shared__ ClArgs sa;
   __shared__ int4 s_grp;
-  extern __shared__ __align__(16) unsigned char dyn[];
+  extern __shared__ __align__(128) unsigned char dyn[];
   if (threadIdx.x == 0) {
+    mbar_init(&s.mbar, 1);
+    s.mb_phase = 0;
     s_grp = make_int4(0, 0, 0, 0);
     for (int g = 0; g < ngroups; ++g) {
       const int4 gr = groups[g];

@@ -19,7 +19,7 @@ enum CtrlSlot {
   CTRL_ROUNDS = 4,       // split rounds of the last clustering
   CTRL_RANKDEF = 5,      // 1 if the last fit dropped eigenvalues of A (truncated pseudo-inverse)
   CTRL_BARRIER = 8,      // grid barrier: arrival counter
-  CTRL_BARRIER_GEN = 9,  // grid barrier: generation
+  CTRL_BARRIER_GEN = 9,  // reserved (zeroed with the barrier counter)
   CTRL_WORDS = 16
 };
 

@@ -22,7 +22,7 @@ namespace clus {
 namespace {
 
 struct Layout {
-  size_t perm, perm2, X, X2, side, marg, d32, nodes, node_sum, pf, pi, pd, pdd, px, chunk_cnt, trace, fin,
+  size_t perm, perm2, X, X2, side, marg, d32, nodes, node_sum, pf, pi, pd, pdd, px, chunk_cnt, trace, arrive, sout, gcen, gacc,
       tab, grp, ord, total;
 };
 
@@ -44,14 +44,17 @@ Layout layout(int N, int rho, int G) {
   L.d32 = take(sizeof(float) * (size_t)N);
   L.nodes = take(sizeof(NodeRec) * MAXNODES);
   L.node_sum = take(sizeof(double) * MAXNODES * (size_t)rho);
-  L.pf = take(sizeof(float) * 2 * (size_t)G * MAXSEG * (rho + 1));
+  L.pf = take(sizeof(float) * (size_t)G * MAXSEG * record_floats(rho));
   L.pi = take(sizeof(int) * (size_t)G * MAXSEG * 2);
   L.pd = take(sizeof(float) * (size_t)G * MAXSEG);
   L.pdd = take(sizeof(double) * (size_t)G * MAXSEG);
   L.px = take(sizeof(int) * (size_t)G * MAXSEG);
   L.chunk_cnt = take(sizeof(int) * maxchunks);
   L.trace = take(sizeof(long long) * (1 + 2 * TRACE_CAP));
-  L.fin = take(sizeof(double) * MAXACT * (size_t)(rho + 2));
+  L.arrive = take(sizeof(unsigned) * MAXACT);
+  L.sout = take(sizeof(SlotOut) * MAXACT);
+  L.gcen = take(sizeof(double) * MAXACT * 2 * (size_t)rho);
+  L.gacc = take(sizeof(double) * MAXACT * (size_t)rho);
   L.tab = take(sizeof(ClArgs));
   L.grp = take(sizeof(int4));
   L.ord = take(sizeof(int));
@@ -64,6 +67,7 @@ Layout layout(int N, int rho, int G) {
 int grid_blocks(int dev) {
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms > MAXG) sms = MAXG;
   return sms > 0 ? sms : 1;   // one block per SM (co-residency of a cooperative launch)
 }
 
@@ -102,7 +106,10 @@ ClArgs make_args(void* ws, int N, int rho, int K, int G, int* ctrl, float* mu, d
   a.px = (int*)(w + L.px);
   a.chunk_cnt = (int*)(w + L.chunk_cnt);
   a.trace = (long long*)(w + L.trace);
-  a.fin = (double*)(w + L.fin);
+  a.arrive = (unsigned*)(w + L.arrive);
+  a.sout = (SlotOut*)(w + L.sout);
+  a.gcen = (double*)(w + L.gcen);
+  a.gacc = (double*)(w + L.gacc);
   return a;
 }
 
@@ -173,6 +180,7 @@ cudaError_t cluster_trace(hdf_handle* h, long long* host, int cap, int* count, c
   cudaError_t e = cudaMemcpyAsync(&n, t, sizeof(n), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return e;
+  if (n > clus::TRACE_CAP) n = clus::TRACE_CAP;
   if (n > cap) n = cap;
   if (n > 0) {
     e = cudaMemcpyAsync(host, t + 1, sizeof(long long) * 2 * (size_t)n, cudaMemcpyDeviceToHost, st);

@@ -27,7 +27,7 @@ constexpr double ROUND_UP = 1.0 + 1.0 / 1048576.0;
 // Events 9 and up are recorded by block 0 between barriers (its own progress).
 enum TracePhase { TR_ROOT = 1, TR_DIST1 = 2, TR_NODE = 4, TR_LLOYD = 5, TR_COUNT = 6,
                   TR_SCATTER = 7, TR_CHILD = 8, TR_LPASS = 9, TR_LUPDATE = 11,
-                  TR_FWAIT = 12, TR_FSTAGE = 13, TR_FDONE = 14 };
+                  TR_FWAIT = 12, TR_FSTAGE = 13, TR_FDONE = 14, TR_SETUP = 15, TR_DPASS = 16 };
 
 struct NodeRec {
   int start, count;   // segment of the permutation

@@ -804,30 +804,78 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
             seg_first_chunk = -1;
           });
     }
+    trace_event(a.trace, a.bid, s.tr_n, TR_DPASS);
     if (!grid_barrier(a, gen, s, TR_DIST1)) return false;
     {
-      auto ncf = [&](int seg) { return s.seg_on[seg] ? contrib_count(a, s, seg) : 0; };
-      auto off = [&](int seg, int i) { return (size_t)contrib_block(a, s, seg, i) * MAXSEG + seg; };
-      replay<8>(s.nseg, -1.0f, ncf, [&](int seg, int i) { return __ldcg(a.pd + off(seg, i)); },
-          [](float x, float y) { return fmaxf(x, y); }, [&](int seg, float m) { s.segmax[seg] = m; });
-      replay<8>(s.nseg, F2{0.0f, 0.0f}, ncf,
-          [&](int seg, int i) {
-            const float* q = a.pf + off(seg, i) * PS;
-            return F2{__ldcg(q), __ldcg(q + 1)};
-          },
-          [](F2 x, F2 y) { return f2_add(x, y); }, [&](int seg, F2 t) { s.segsse[seg] = f2_to_d(t); });
-      ArgMax none;
-      none.d = -1.0;
-      none.i = 0x7fffffff;
-      replay<8>(s.nseg, none, ncf,
-          [&](int seg, int i) {
-            ArgMax r;
-            r.d = __ldcg(a.pdd + off(seg, i));
-            r.i = __ldcg(a.px + off(seg, i));
-            return r;
-          },
-          [](ArgMax x, ArgMax y) { return better(y.d, y.i, x.d, x.i) ? y : x; },
-          [&](int seg, ArgMax r) { s.segarg[seg] = r.i; });
+      // One fused replay of the blocks' maxima, SSE and FP64 arg-maxima: warp
+      // per segment, lanes over the contributors (all loads of a lane issued
+      // together), xor trees; every block computes the same values.
+      constexpr int MAXC = (MAXG + 31) / 32;
+      const int lane = tid & 31, warp = tid >> 5;
+      for (int seg = warp; seg < s.nseg; seg += CL_WARPS) {
+        if (!s.seg_on[seg]) {
+          if (lane == 0) {
+            s.segmax[seg] = -1.0f;
+            s.segsse[seg] = 0.0;
+            s.segarg[seg] = 0x7fffffff;
+          }
+          continue;
+        }
+        const int nc = contrib_count(a, s, seg);
+        float m = -1.0f;
+        F2 t{0.0f, 0.0f};
+        ArgMax r;
+        r.d = -1.0;
+        r.i = 0x7fffffff;
+        {
+          float pm[MAXC], ph[MAXC], pl[MAXC];
+#pragma unroll
+          for (int k = 0; k < MAXC; ++k) {
+            const int c = lane + 32 * k;
+            if (c < nc) {
+              const size_t o = (size_t)contrib_block(a, s, seg, c) * MAXSEG + seg;
+              pm[k] = __ldcg(a.pd + o);
+              ph[k] = __ldcg(a.pf + o * PS);
+              pl[k] = __ldcg(a.pf + o * PS + 1);
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < MAXC; ++k) {
+            if (lane + 32 * k < nc) {
+              m = fmaxf(m, pm[k]);
+              t = f2_add(t, F2{ph[k], pl[k]});
+            }
+          }
+        }
+        {
+          double pd[MAXC];
+          int px[MAXC];
+#pragma unroll
+          for (int k = 0; k < MAXC; ++k) {
+            const int c = lane + 32 * k;
+            if (c < nc) {
+              const size_t o = (size_t)contrib_block(a, s, seg, c) * MAXSEG + seg;
+              pd[k] = __ldcg(a.pdd + o);
+              px[k] = __ldcg(a.px + o);
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < MAXC; ++k)
+            if (lane + 32 * k < nc && better(pd[k], px[k], r.d, r.i)) { r.d = pd[k]; r.i = px[k]; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+          t = f2_add(t, shfl_xor_t(t, o));
+          const ArgMax q = shfl_xor_t(r, o);
+          if (better(q.d, q.i, r.d, r.i)) r = q;
+        }
+        if (lane == 0) {
+          s.segmax[seg] = m;
+          s.segsse[seg] = f2_to_d(t);
+          s.segarg[seg] = r.i;
+        }
+      }
     }
     __syncthreads();
     return true;
@@ -866,7 +914,10 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
     if (tid == 0) {
       s.nslots = s.nneeded;
       s.nseg = s.nneeded;
-      for (int i = 0; i < s.nneeded; ++i) {
+    }
+    {   // one thread per slot: its node's loads are independent of the others'
+      const int i = tid;
+      if (i < s.nneeded) {
         const int nd = s.needed[i];
         SlotRec& sl = s.slot[i];
         sl.node = nd;
@@ -888,6 +939,7 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
     }
     __syncthreads();
     build_chunks(s);
+    trace_event(a.trace, a.bid, s.tr_n, TR_SETUP);
     for (int v = tid; v < s.nslots * rho; v += CL_THREADS) {
       const int sl = v / rho, d = v % rho;
       const float x = guide_at(a, (size_t)d * N + s.slot[sl].a_idx);
@@ -1213,8 +1265,12 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
             },
             [&](int seg) {
               const size_t off = (size_t)bid * MAXSEG + seg;
-              block_sum_f2<RMAX>(hi, lo, rho, s, a.pf + off * PS);
-              block_sum_i2(cnt, chg, s, reinterpret_cast<int*>(a.pf + off * PS + 2 * rho));
+              if (__syncthreads_or(cnt != 0 || chg != 0)) {
+                block_sum_f2<RMAX>(hi, lo, rho, s, a.pf + off * PS);
+                block_sum_i2(cnt, chg, s, reinterpret_cast<int*>(a.pf + off * PS + 2 * rho));
+              } else {   // nothing moved to or from side b here: a zero record
+                for (int v = tid; v < PS; v += CL_THREADS) a.pf[off * PS + v] = 0.0f;
+              }
 #pragma unroll
               for (int d = 0; d < RMAX; ++d) hi[d] = lo[d] = 0.0f;
               cnt = 0;
@@ -1436,14 +1492,12 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
 
   // ------------------------------------------------------------ outputs
   // Leaves of the final replay are the clusters; s.leaf_cl holds the index.
-  if (tid == 0) {
-    s.nseg = s.nleaves;
-    for (int i = 0; i < s.nleaves; ++i) {
-      const int nd = s.leaf_node[i];
-      s.seg_start[i] = __ldcg(&a.nodes[nd].start);
-      s.seg_count[i] = __ldcg(&a.nodes[nd].count);
-      s.seg_on[i] = 1;
-    }
+  if (tid == 0) s.nseg = s.nleaves;
+  for (int i = tid; i < s.nleaves; i += CL_THREADS) {
+    const int nd = s.leaf_node[i];
+    s.seg_start[i] = __ldcg(&a.nodes[nd].start);
+    s.seg_count[i] = __ldcg(&a.nodes[nd].count);
+    s.seg_on[i] = 1;
   }
   __syncthreads();
   if (bid == 0) {
@@ -1453,11 +1507,12 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
       a.mu64[s.leaf_cl[i] * rho + d] = m;
       a.mu[s.leaf_cl[i] * rho + d] = (float)m;
     }
+    for (int i = tid; i < s.nleaves; i += CL_THREADS)   // SSE of the leaves by cluster index
+      s.sim_sse[s.leaf_cl[i]] = __ldcg(&a.nodes[s.leaf_node[i]].sse);
+    __syncthreads();
     if (tid == 0) {
       double ek = 0.0;
-      for (int c = 0; c < s.nleaves; ++c)
-        for (int i = 0; i < s.nleaves; ++i)
-          if (s.leaf_cl[i] == c) ek += __ldcg(&a.nodes[s.leaf_node[i]].sse);
+      for (int c = 0; c < s.nleaves; ++c) ek += s.sim_sse[c];
       *a.ek = ek;
       a.ctrl[CTRL_K_EFF] = s.nclusters;
       a.ctrl[CTRL_LLOYD_MAX] = lloyd_max;

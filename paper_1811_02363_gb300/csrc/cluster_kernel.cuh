@@ -611,6 +611,191 @@ __host__ __device__ constexpr size_t dyn_smem_bytes(int rho) {
          sizeof(float) * ((size_t)MAXG * record_floats(rho) + 2 * CL_THREADS);
 }
 
+// Distance statistics of every segment of the table against the centres
+// c32[seg] / c64[seg]: SSE, then the farthest point decided in FP64 among
+// the FP32 candidates (ties -> lowest raster index).  Results in s.segmax /
+// s.segsse / s.segarg.  `from_scratch` reads the points (and raster
+// indices) from the scatter buffers and moves them into place.  One grid
+// barrier: each block takes its own FP64
+// candidates relative to its own FP32 maximum; the global FP64 maximiser
+// lies within 2^-12 of the global FP32 maximum, hence of its block's
+// maximum, so it is its block's winner and the replay of the block winners
+// returns it.
+template <int RMAX>
+__device__ __noinline__ bool dist_stats_fn(const ClArgs& a, ClShared& s, unsigned& gen,
+                                           const float* c32, const double* c64, float* X,
+                                           const float* Xn, uint32_t* P, const uint32_t* Pn,
+                                           bool from_scratch) {
+  constexpr int UB = RMAX <= 4 ? 8 : (RMAX <= 8 ? 4 : (RMAX <= 32 ? 2 : 1));
+  const int rho = a.rho;
+  const int PS = record_floats(rho);
+  const int tid = threadIdx.x, bid = a.bid;
+  const size_t N = (size_t)a.N;
+
+  {
+    float mx = -1.0f;
+    F2 sse{0.0f, 0.0f};
+    int seg_first_chunk = -1;
+    for_blocks(a, s,
+        [&](int seg, int base, int end, int j) {
+          if (seg_first_chunk < 0) seg_first_chunk = j;
+          const float* c = c32 + seg * rho;
+#pragma unroll
+          for (int u0 = 0; u0 < PPT; u0 += UB) {
+            float x[UB][RMAX];
+            uint32_t pid[UB];
+            const float* src = from_scratch ? Xn : X;
+#pragma unroll
+            for (int b = 0; b < UB; ++b) {
+              const int pos = base + (u0 + b) * CL_THREADS + tid;
+              const bool v = pos < end;
+              pid[b] = (v && from_scratch) ? __ldcg(Pn + pos) : 0u;
+#pragma unroll
+              for (int d = 0; d < RMAX; ++d)
+                x[b][d] = (v && d < rho) ? __ldcg(src + (size_t)d * N + pos) : 0.0f;
+            }
+#pragma unroll
+            for (int b = 0; b < UB; ++b) {
+              const int pos = base + (u0 + b) * CL_THREADS + tid;
+              if (pos >= end) continue;
+              float d2 = 0.0f;
+#pragma unroll
+              for (int d = 0; d < RMAX; ++d) {
+                if (d < rho) {
+                  if (from_scratch) X[(size_t)d * N + pos] = x[b][d];
+                  const float t = x[b][d] - c[d];
+                  d2 = fmaf(t, t, d2);
+                }
+              }
+              if (from_scratch) P[pos] = pid[b];
+              a.d32[pos] = d2;
+              mx = fmaxf(mx, d2);
+              two_sum_acc(sse.hi, sse.lo, d2);
+            }
+          }
+        },
+        [&](int seg) {
+          const size_t off = (size_t)bid * MAXSEG + seg;
+          block_max_sum(mx, sse, s, a.pd + off, a.pf + off * PS);   // ends with a block sync
+          const float m = s.bmax;                                   // this block's maximum
+          // FP64 candidates of this block's chunks of the segment
+          double bd = -1.0;
+          int bi = 0x7fffffff;
+          for (int j = seg_first_chunk; j < s.seg_chunk0[seg + 1]; j += a.G) {
+            const int base = s.seg_start[seg] + (j - s.seg_chunk0[seg]) * CH;
+            const int end = s.seg_start[seg] + s.seg_count[seg];
+            float dd[PPT];
+#pragma unroll
+            for (int u = 0; u < PPT; ++u) {
+              const int pos = base + u * CL_THREADS + tid;
+              dd[u] = (pos < end) ? __ldcg(a.d32 + pos) : -1.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < PPT; ++u) {
+              const int pos = base + u * CL_THREADS + tid;
+              if (pos >= end) continue;
+              if (m > 0.0f && dd[u] < m * (1.0f - CAND_REL)) continue;
+              const int idx = (int)__ldcg(P + pos);
+              double e = 0.0;
+              if (m > 0.0f) {
+                const double* cc = c64 + (size_t)seg * rho;
+                float xv[RMAX];
+#pragma unroll
+                for (int d = 0; d < RMAX; ++d) xv[d] = (d < rho) ? xat(X, N, d, pos) : 0.0f;
+#pragma unroll
+                for (int d = 0; d < RMAX; ++d) {
+                  if (d < rho) {
+                    const double t = (double)xv[d] - cc[d];
+                    e = fma(t, t, e);
+                  }
+                }
+              }
+              if (better(e, idx, bd, bi)) { bd = e; bi = idx; }
+            }
+          }
+          block_argmax(bd, bi, s, a.pdd + off, a.px + off);
+          mx = -1.0f;
+          sse = F2{0.0f, 0.0f};
+          seg_first_chunk = -1;
+        });
+  }
+  trace_event(a.trace, a.bid, s.tr_n, TR_DPASS);
+  if (!grid_barrier(a, gen, s, TR_DIST1)) return false;
+  {
+    // One fused replay of the blocks' maxima, SSE and FP64 arg-maxima: warp
+    // per segment, lanes over the contributors (all loads of a lane issued
+    // together), xor trees; every block computes the same values.
+    constexpr int MAXC = (MAXG + 31) / 32;
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int seg = warp; seg < s.nseg; seg += CL_WARPS) {
+      if (!s.seg_on[seg]) {
+        if (lane == 0) {
+          s.segmax[seg] = -1.0f;
+          s.segsse[seg] = 0.0;
+          s.segarg[seg] = 0x7fffffff;
+        }
+        continue;
+      }
+      const int nc = contrib_count(a, s, seg);
+      float m = -1.0f;
+      F2 t{0.0f, 0.0f};
+      ArgMax r;
+      r.d = -1.0;
+      r.i = 0x7fffffff;
+      {
+        float pm[MAXC], ph[MAXC], pl[MAXC];
+#pragma unroll
+        for (int k = 0; k < MAXC; ++k) {
+          const int c = lane + 32 * k;
+          if (c < nc) {
+            const size_t o = (size_t)contrib_block(a, s, seg, c) * MAXSEG + seg;
+            pm[k] = __ldcg(a.pd + o);
+            ph[k] = __ldcg(a.pf + o * PS);
+            pl[k] = __ldcg(a.pf + o * PS + 1);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < MAXC; ++k) {
+          if (lane + 32 * k < nc) {
+            m = fmaxf(m, pm[k]);
+            t = f2_add(t, F2{ph[k], pl[k]});
+          }
+        }
+      }
+      {
+        double pd[MAXC];
+        int px[MAXC];
+#pragma unroll
+        for (int k = 0; k < MAXC; ++k) {
+          const int c = lane + 32 * k;
+          if (c < nc) {
+            const size_t o = (size_t)contrib_block(a, s, seg, c) * MAXSEG + seg;
+            pd[k] = __ldcg(a.pdd + o);
+            px[k] = __ldcg(a.px + o);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < MAXC; ++k)
+          if (lane + 32 * k < nc && better(pd[k], px[k], r.d, r.i)) { r.d = pd[k]; r.i = px[k]; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        t = f2_add(t, shfl_xor_t(t, o));
+        const ArgMax q = shfl_xor_t(r, o);
+        if (better(q.d, q.i, r.d, r.i)) r = q;
+      }
+      if (lane == 0) {
+        s.segmax[seg] = m;
+        s.segsse[seg] = f2_to_d(t);
+        s.segarg[seg] = r.i;
+      }
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
 // The clustering of one guide by the blocks of its group.
 template <int RMAX>
 __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
@@ -706,179 +891,8 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
       });
   __syncthreads();
 
-  // Distance statistics of every segment of the table against the centres
-  // c32[seg] / c64[seg]: SSE, then the farthest point decided in FP64 among
-  // the FP32 candidates (ties -> lowest raster index).  Results in s.segmax /
-  // s.segsse / s.segarg.  `from_scratch` reads the points (and raster
-  // indices) from the scatter buffers and moves them into place.  One grid
-  // barrier: each block takes its own FP64
-  // candidates relative to its own FP32 maximum; the global FP64 maximiser
-  // lies within 2^-12 of the global FP32 maximum, hence of its block's
-  // maximum, so it is its block's winner and the replay of the block winners
-  // returns it.
   auto dist_stats = [&](bool from_scratch) -> bool {
-    {
-      float mx = -1.0f;
-      F2 sse{0.0f, 0.0f};
-      int seg_first_chunk = -1;
-      for_blocks(a, s,
-          [&](int seg, int base, int end, int j) {
-            if (seg_first_chunk < 0) seg_first_chunk = j;
-            const float* c = c32 + seg * rho;
-#pragma unroll
-            for (int u0 = 0; u0 < PPT; u0 += UB) {
-              float x[UB][RMAX];
-              uint32_t pid[UB];
-              const float* src = from_scratch ? Xn : X;
-#pragma unroll
-              for (int b = 0; b < UB; ++b) {
-                const int pos = base + (u0 + b) * CL_THREADS + tid;
-                const bool v = pos < end;
-                pid[b] = (v && from_scratch) ? __ldcg(Pn + pos) : 0u;
-#pragma unroll
-                for (int d = 0; d < RMAX; ++d)
-                  x[b][d] = (v && d < rho) ? __ldcg(src + (size_t)d * N + pos) : 0.0f;
-              }
-#pragma unroll
-              for (int b = 0; b < UB; ++b) {
-                const int pos = base + (u0 + b) * CL_THREADS + tid;
-                if (pos >= end) continue;
-                float d2 = 0.0f;
-#pragma unroll
-                for (int d = 0; d < RMAX; ++d) {
-                  if (d < rho) {
-                    if (from_scratch) X[(size_t)d * N + pos] = x[b][d];
-                    const float t = x[b][d] - c[d];
-                    d2 = fmaf(t, t, d2);
-                  }
-                }
-                if (from_scratch) P[pos] = pid[b];
-                a.d32[pos] = d2;
-                mx = fmaxf(mx, d2);
-                two_sum_acc(sse.hi, sse.lo, d2);
-              }
-            }
-          },
-          [&](int seg) {
-            const size_t off = (size_t)bid * MAXSEG + seg;
-            block_max_sum(mx, sse, s, a.pd + off, a.pf + off * PS);   // ends with a block sync
-            const float m = s.bmax;                                   // this block's maximum
-            // FP64 candidates of this block's chunks of the segment
-            double bd = -1.0;
-            int bi = 0x7fffffff;
-            for (int j = seg_first_chunk; j < s.seg_chunk0[seg + 1]; j += a.G) {
-              const int base = s.seg_start[seg] + (j - s.seg_chunk0[seg]) * CH;
-              const int end = s.seg_start[seg] + s.seg_count[seg];
-              float dd[PPT];
-#pragma unroll
-              for (int u = 0; u < PPT; ++u) {
-                const int pos = base + u * CL_THREADS + tid;
-                dd[u] = (pos < end) ? __ldcg(a.d32 + pos) : -1.0f;
-              }
-#pragma unroll
-              for (int u = 0; u < PPT; ++u) {
-                const int pos = base + u * CL_THREADS + tid;
-                if (pos >= end) continue;
-                if (m > 0.0f && dd[u] < m * (1.0f - CAND_REL)) continue;
-                const int idx = (int)__ldcg(P + pos);
-                double e = 0.0;
-                if (m > 0.0f) {
-                  const double* cc = c64 + (size_t)seg * rho;
-                  float xv[RMAX];
-#pragma unroll
-                  for (int d = 0; d < RMAX; ++d) xv[d] = (d < rho) ? xat(X, N, d, pos) : 0.0f;
-#pragma unroll
-                  for (int d = 0; d < RMAX; ++d) {
-                    if (d < rho) {
-                      const double t = (double)xv[d] - cc[d];
-                      e = fma(t, t, e);
-                    }
-                  }
-                }
-                if (better(e, idx, bd, bi)) { bd = e; bi = idx; }
-              }
-            }
-            block_argmax(bd, bi, s, a.pdd + off, a.px + off);
-            mx = -1.0f;
-            sse = F2{0.0f, 0.0f};
-            seg_first_chunk = -1;
-          });
-    }
-    trace_event(a.trace, a.bid, s.tr_n, TR_DPASS);
-    if (!grid_barrier(a, gen, s, TR_DIST1)) return false;
-    {
-      // One fused replay of the blocks' maxima, SSE and FP64 arg-maxima: warp
-      // per segment, lanes over the contributors (all loads of a lane issued
-      // together), xor trees; every block computes the same values.
-      constexpr int MAXC = (MAXG + 31) / 32;
-      const int lane = tid & 31, warp = tid >> 5;
-      for (int seg = warp; seg < s.nseg; seg += CL_WARPS) {
-        if (!s.seg_on[seg]) {
-          if (lane == 0) {
-            s.segmax[seg] = -1.0f;
-            s.segsse[seg] = 0.0;
-            s.segarg[seg] = 0x7fffffff;
-          }
-          continue;
-        }
-        const int nc = contrib_count(a, s, seg);
-        float m = -1.0f;
-        F2 t{0.0f, 0.0f};
-        ArgMax r;
-        r.d = -1.0;
-        r.i = 0x7fffffff;
-        {
-          float pm[MAXC], ph[MAXC], pl[MAXC];
-#pragma unroll
-          for (int k = 0; k < MAXC; ++k) {
-            const int c = lane + 32 * k;
-            if (c < nc) {
-              const size_t o = (size_t)contrib_block(a, s, seg, c) * MAXSEG + seg;
-              pm[k] = __ldcg(a.pd + o);
-              ph[k] = __ldcg(a.pf + o * PS);
-              pl[k] = __ldcg(a.pf + o * PS + 1);
-            }
-          }
-#pragma unroll
-          for (int k = 0; k < MAXC; ++k) {
-            if (lane + 32 * k < nc) {
-              m = fmaxf(m, pm[k]);
-              t = f2_add(t, F2{ph[k], pl[k]});
-            }
-          }
-        }
-        {
-          double pd[MAXC];
-          int px[MAXC];
-#pragma unroll
-          for (int k = 0; k < MAXC; ++k) {
-            const int c = lane + 32 * k;
-            if (c < nc) {
-              const size_t o = (size_t)contrib_block(a, s, seg, c) * MAXSEG + seg;
-              pd[k] = __ldcg(a.pdd + o);
-              px[k] = __ldcg(a.px + o);
-            }
-          }
-#pragma unroll
-          for (int k = 0; k < MAXC; ++k)
-            if (lane + 32 * k < nc && better(pd[k], px[k], r.d, r.i)) { r.d = pd[k]; r.i = px[k]; }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-          t = f2_add(t, shfl_xor_t(t, o));
-          const ArgMax q = shfl_xor_t(r, o);
-          if (better(q.d, q.i, r.d, r.i)) r = q;
-        }
-        if (lane == 0) {
-          s.segmax[seg] = m;
-          s.segsse[seg] = f2_to_d(t);
-          s.segarg[seg] = r.i;
-        }
-      }
-    }
-    __syncthreads();
-    return true;
+    return dist_stats_fn<RMAX>(a, s, gen, c32, c64, X, Xn, P, Pn, from_scratch);
   };
 
   if (!dist_stats(false)) return;

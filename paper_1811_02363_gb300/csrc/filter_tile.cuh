@@ -73,13 +73,46 @@ struct TileCfg {
   static_assert(LD >= HC, "row stride must hold the halo");
 };
 
+// XW outputs of the row FIR omega_1 (*) u on one halo row, u = b (plane 0)
+// or b f (the other planes), from 16-byte-aligned shared rows; results to out.
+template <int SB, int XW>
+__device__ __forceinline__ void fir_row(const float* __restrict__ brow, const float* __restrict__ frow,
+                                        bool plane0, const Taps& taps, float* __restrict__ out) {
+  constexpr int NIN4 = (XW + 2 * SB + 3) / 4, NTAP = 2 * SB + 1;
+  const float4* pb = reinterpret_cast<const float4*>(brow);
+  const float4* pf = reinterpret_cast<const float4*>(frow);
+  float in[4 * NIN4];
+#pragma unroll
+  for (int t = 0; t < NIN4; ++t) {
+    const float4 b = pb[t];
+    if (plane0) {
+      in[4 * t] = b.x; in[4 * t + 1] = b.y; in[4 * t + 2] = b.z; in[4 * t + 3] = b.w;
+    } else {
+      const float4 v = pf[t];
+      in[4 * t] = b.x * v.x; in[4 * t + 1] = b.y * v.y;
+      in[4 * t + 2] = b.z * v.z; in[4 * t + 3] = b.w * v.w;
+    }
+  }
+  float h[XW];
+#pragma unroll
+  for (int o = 0; o < XW; ++o) h[o] = 0.0f;
+#pragma unroll
+  for (int t = 0; t < NTAP; ++t) {
+#pragma unroll
+    for (int o = 0; o < XW; ++o) h[o] = fmaf(taps.w[t], in[o + t], h[o]);
+  }
+  float4* ph = reinterpret_cast<float4*>(out);
+#pragma unroll
+  for (int o = 0; o < XW / 4; ++o) ph[o] = make_float4(h[4 * o], h[4 * o + 1], h[4 * o + 2], h[4 * o + 3]);
+}
+
 template <int SB, int P, int TY>
 __global__ void __launch_bounds__(512, 1)
 filter_tile_kernel(const FilterArgs a, const Taps taps) {
   using Cfg = TileCfg<SB, P, TY>;
   constexpr int TX = Cfg::TX, NT = Cfg::NT, YV = Cfg::YV, XH = Cfg::XH, NSEG = Cfg::NSEG;
   constexpr int HR = Cfg::HR, HC = Cfg::HC, LD = Cfg::LD, LDH = Cfg::LDH;
-  constexpr int NIN4 = Cfg::NIN4, NTAP = 2 * SB + 1;
+  constexpr int NTAP = 2 * SB + 1;
   extern __shared__ __align__(16) float sm[];
   float* sF = sm;                        // [P][HR][LD] image channels of the chunk
   float* sB0 = sF + Cfg::SF;             // [2][HR][LD] b_k, double-buffered
@@ -100,35 +133,56 @@ filter_tile_kernel(const FilterArgs a, const Taps taps) {
   const int gx = x0 + xv;
   const int qgv = chunk * P + qv;        // global plane of this thread's column run
 
-  // ---- stage the image channels of this chunk and b_0 (cp.async, zero outside)
-  for (int idx = tid; idx < P * HR * HC; idx += NT) {
-    const int q = idx / (HR * HC);
-    const int r = (idx / HC) % HR;
-    const int c = idx % HC;
-    const int ch = chunk * P + q - 1;
-    const int yy = y0 - SB + r, xx = x0 - SB + c;
-    const bool ok = ch >= 0 && ch < n && yy >= 0 && yy < H && xx >= 0 && xx < W;
-    cp_async4(sF + (q * HR + r) * LD + c, ok ? a.f + (size_t)ch * N + (size_t)yy * W + xx : a.f, ok);
+  // ---- staging (cp.async, zero-filled outside the image): a warp copies
+  // whole halo rows, lanes over the columns, so the per-element index math is
+  // a compare and an add.  The column bounds of a lane do not change.
+  const int lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = NT / 32;
+  constexpr int CPL = (HC + 31) / 32;   // columns per lane
+  unsigned col_ok = 0;                  // bit j: column lane + 32 j inside the image
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) {
+    const int c = lane + 32 * j, xx = x0 - SB + c;
+    if (c < HC && xx >= 0 && xx < W) col_ok |= 1u << j;
   }
-  auto stage_b = [&](int k, float* dst) {
-    const float* Bk = a.B + (size_t)k * N;
-    for (int idx = tid; idx < HR * HC; idx += NT) {
-      const int r = idx / HC, c = idx % HC;
-      const int yy = y0 - SB + r, xx = x0 - SB + c;
-      const bool ok = yy >= 0 && yy < H && xx >= 0 && xx < W;
-      cp_async4(dst + r * LD + c, ok ? Bk + (size_t)yy * W + xx : Bk, ok);
+  auto stage_rows = [&](const float* plane, float* dst, int r0, int nrows) {
+    for (int r = r0; r < nrows; r += NW) {
+      const int yy = y0 - SB + r;
+      const bool rok = yy >= 0 && yy < H;
+      const float* grow = plane + (ptrdiff_t)yy * W + (x0 - SB);
+      float* srow = dst + r * LD;
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) {
+        const int c = lane + 32 * j;
+        if (c < HC) {
+          const bool ok = rok && ((col_ok >> j) & 1u);
+          cp_async4(srow + c, ok ? grow + c : plane, ok);
+        }
+      }
     }
   };
+  for (int q = 0; q < P; ++q) {
+    const int ch = chunk * P + q - 1;
+    if (ch >= 0 && ch < n) {
+      stage_rows(a.f + (size_t)ch * N, sF + q * HR * LD, warp, HR);
+    } else {
+      for (int i = tid; i < HR * LD; i += NT) sF[q * HR * LD + i] = 0.0f;
+    }
+  }
+  auto stage_b = [&](int k, float* dst) { stage_rows(a.B + (size_t)k * N, dst, warp, HR); };
   stage_b(0, sB0);
   cp_async_commit();
   for (int i = tid; i < Cfg::SR; i += NT) sR[i] = 0.0f;
 
   float acc[YV], cnext[YV];
+  // c_k at this thread's pixels: rows yv0 .. yv0 + YV - 1 of column gx
+  const bool colin = gx < W;
+  const int nrow_in = colin ? max(0, min(YV, H - (y0 + yv0))) : 0;
+  const float* cptr = a.C + (size_t)(y0 + yv0) * W + gx;   // dereferenced for rows < nrow_in only
 #pragma unroll
   for (int o = 0; o < YV; ++o) {
     acc[o] = 0.0f;
-    const int gy = y0 + yv0 + o;
-    cnext[o] = (gy < H && gx < W) ? __ldg(a.C + (size_t)gy * W + gx) : 0.0f;
+    cnext[o] = (o < nrow_in) ? __ldg(cptr + (size_t)o * W) : 0.0f;
   }
 
   for (int k = 0; k < K; ++k) {
@@ -138,45 +192,42 @@ filter_tile_kernel(const FilterArgs a, const Taps taps) {
     cp_async_wait<1>();                  // everything but b_{k+1} has landed
     __syncthreads();
     float ccur[YV];
+    cptr += N;
+    const int nnext = (k + 1 < K) ? nrow_in : 0;
 #pragma unroll
     for (int o = 0; o < YV; ++o) {
       ccur[o] = cnext[o];
-      const int gy = y0 + yv0 + o;
-      cnext[o] = (k + 1 < K && gy < H && gx < W)
-                     ? __ldg(a.C + (size_t)(k + 1) * N + (size_t)gy * W + gx) : 0.0f;
+      cnext[o] = (o < nnext) ? __ldg(cptr + (size_t)o * W) : 0.0f;
     }
-    // ---- row pass over every halo row: H = omega_1 (*) (b_k f)
-    for (int task = tid; task < P * HR * NSEG; task += NT) {
-      const int q = task / (HR * NSEG);
-      const int rem = task % (HR * NSEG);
-      const int r = rem / NSEG, seg = rem % NSEG;
-      const int qg = chunk * P + q;
-      if (qg > n) continue;
-      const float4* pb = reinterpret_cast<const float4*>(sB + r * LD + seg * XH);
-      const float4* pf = reinterpret_cast<const float4*>(sF + (q * HR + r) * LD + seg * XH);
-      float in[4 * NIN4];
-#pragma unroll
-      for (int t = 0; t < NIN4; ++t) {
-        const float4 b = pb[t];
-        if (qg == 0) {
-          in[4 * t] = b.x; in[4 * t + 1] = b.y; in[4 * t + 2] = b.z; in[4 * t + 3] = b.w;
-        } else {
-          const float4 v = pf[t];
-          in[4 * t] = b.x * v.x; in[4 * t + 1] = b.y * v.y;
-          in[4 * t + 2] = b.z * v.z; in[4 * t + 3] = b.w * v.w;
-        }
+    // ---- row pass over every halo row: H = omega_1 (*) (b_k f).  Tasks of
+    // XH outputs fill whole rounds of the block; the remainder is split into
+    // tasks of XH / 2 outputs, so that the last round keeps every thread busy.
+    {
+      constexpr int T = P * HR * NSEG;
+      constexpr int FULL = (T / NT) * NT;
+      auto task_rows = [&](int task, int& q, int& r, int& seg) {
+        q = task / (HR * NSEG);
+        const int rem = task - q * (HR * NSEG);
+        r = rem / NSEG;
+        seg = rem - r * NSEG;
+      };
+      for (int task = tid; task < FULL; task += NT) {
+        int q, r, seg;
+        task_rows(task, q, r, seg);
+        const int qg = chunk * P + q;
+        if (qg > n) continue;
+        fir_row<SB, XH>(sB + r * LD + seg * XH, sF + (q * HR + r) * LD + seg * XH, qg == 0, taps,
+                        sH + (q * HR + r) * LDH + seg * XH);
       }
-      float h[XH];
-#pragma unroll
-      for (int o = 0; o < XH; ++o) h[o] = 0.0f;
-#pragma unroll
-      for (int t = 0; t < NTAP; ++t) {
-#pragma unroll
-        for (int o = 0; o < XH; ++o) h[o] = fmaf(taps.w[t], in[o + t], h[o]);
+      for (int hk = tid; hk < 2 * (T - FULL); hk += NT) {
+        int q, r, seg;
+        task_rows(FULL + (hk >> 1), q, r, seg);
+        const int qg = chunk * P + q;
+        if (qg > n) continue;
+        const int x = seg * XH + (hk & 1) * (XH / 2);
+        fir_row<SB, XH / 2>(sB + r * LD + x, sF + (q * HR + r) * LD + x, qg == 0, taps,
+                            sH + (q * HR + r) * LDH + x);
       }
-      float4* ph = reinterpret_cast<float4*>(sH + (q * HR + r) * LDH + seg * XH);
-#pragma unroll
-      for (int o = 0; o < XH / 4; ++o) ph[o] = make_float4(h[4 * o], h[4 * o + 1], h[4 * o + 2], h[4 * o + 3]);
     }
     __syncthreads();
     // ---- column pass at the tile's pixels, accumulate c_k V

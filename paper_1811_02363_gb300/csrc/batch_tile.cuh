@@ -61,12 +61,11 @@ __device__ __forceinline__ void batch_tile_item(const BatchImg* __restrict__ imp
                                                 int chunk, float* sm) {
   constexpr int YV = batch_yv(SB);
   constexpr int TX = BT_TX, NT = BT_THREADS, XH = 16, NSEG = TX / XH;
-  constexpr int NIN = XH + 2 * SB, NIN4 = (NIN + 3) / 4;
   constexpr int LD = batch_ld(SB), LDH = round_ld(TX);
   constexpr int NTAP = 2 * SB + 1;
   const int P = imp->P, TY = imp->TY;
   const int H = imp->H, W = imp->W, n = imp->n;
-  const int HR = TY + 2 * SB, HC = TX + 2 * SB;
+  const int HR = TY + 2 * SB;
   const int SBF = HR * LD;
   float* sF = sm;                          // [P][HR][LD]
   float* sB0 = sF + P * SBF;               // [2][HR][LD]
@@ -89,24 +88,40 @@ __device__ __forceinline__ void batch_tile_item(const BatchImg* __restrict__ imp
 #pragma unroll
   for (int t = 0; t <= SB; ++t) wh[t] = __ldg(imp->taps + t);
 
-  for (int idx = tid; idx < P * HR * HC; idx += NT) {
-    const int q = idx / (HR * HC);
-    const int r = (idx / HC) % HR;
-    const int c = idx % HC;
-    const int ch = chunk * P + q - 1;
-    const int yy = y0 - SB + r, xx = x0 - SB + c;
-    const bool ok = ch >= 0 && ch < n && yy >= 0 && yy < H && xx >= 0 && xx < W;
-    cp_async4(sF + (q * HR + r) * LD + c, ok ? f + (size_t)ch * N + (size_t)yy * W + xx : f, ok);
+  // staging (cp.async, zero-filled outside the image): a warp copies whole
+  // halo rows, lanes over the columns (column bounds fixed per lane)
+  const int lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = NT / 32;
+  constexpr int HC = TX + 2 * SB;
+  constexpr int CPL = (HC + 31) / 32;
+  unsigned col_ok = 0;
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) {
+    const int c = lane + 32 * j, xx = x0 - SB + c;
+    if (c < HC && xx >= 0 && xx < W) col_ok |= 1u << j;
   }
-  auto stage_b = [&](int k, float* dst) {
-    const float* Bk = Bp + (size_t)k * N;
-    for (int idx = tid; idx < HR * HC; idx += NT) {
-      const int r = idx / HC, c = idx % HC;
-      const int yy = y0 - SB + r, xx = x0 - SB + c;
-      const bool ok = yy >= 0 && yy < H && xx >= 0 && xx < W;
-      cp_async4(dst + r * LD + c, ok ? Bk + (size_t)yy * W + xx : Bk, ok);
+  auto stage_rows = [&](const float* plane, float* dst) {
+    for (int r = warp; r < HR; r += NW) {
+      const int yy = y0 - SB + r;
+      const bool rok = yy >= 0 && yy < H;
+      const float* grow = plane + (ptrdiff_t)yy * W + (x0 - SB);
+      float* srow = dst + r * LD;
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) {
+        const int c = lane + 32 * j;
+        if (c < HC) {
+          const bool ok = rok && ((col_ok >> j) & 1u);
+          cp_async4(srow + c, ok ? grow + c : plane, ok);
+        }
+      }
     }
   };
+  for (int q = 0; q < P; ++q) {
+    const int ch = chunk * P + q - 1;
+    if (ch >= 0 && ch < n) stage_rows(f + (size_t)ch * N, sF + q * SBF);
+    else for (int i = tid; i < SBF; i += NT) sF[q * SBF + i] = 0.0f;
+  }
+  auto stage_b = [&](int k, float* dst) { stage_rows(Bp + (size_t)k * N, dst); };
   stage_b(0, sB0);
   cp_async_commit();
   for (int i = tid; i < TY * TX; i += NT) sR[i] = 0.0f;
@@ -128,39 +143,35 @@ __device__ __forceinline__ void batch_tile_item(const BatchImg* __restrict__ imp
       ccur[o] = (qgv <= n && gy < H && gx < W) ? __ldg(Cp + (size_t)k * N + (size_t)gy * W + gx)
                                                 : 0.0f;
     }
-    // row pass over every halo row of every plane of the chunk
-    for (int task = tid; task < P * HR * NSEG; task += NT) {
-      const int q = task / (HR * NSEG);
-      const int rem = task - q * (HR * NSEG);
-      const int r = rem / NSEG, seg = rem % NSEG;
-      const int qg = chunk * P + q;
-      if (qg > n) continue;
-      const float4* pb = reinterpret_cast<const float4*>(sB + r * LD + seg * XH);
-      const float4* pf = reinterpret_cast<const float4*>(sF + (q * HR + r) * LD + seg * XH);
-      float in[4 * NIN4];
-#pragma unroll
-      for (int t = 0; t < NIN4; ++t) {
-        const float4 b = pb[t];
-        if (qg == 0) {
-          in[4 * t] = b.x; in[4 * t + 1] = b.y; in[4 * t + 2] = b.z; in[4 * t + 3] = b.w;
-        } else {
-          const float4 v = pf[t];
-          in[4 * t] = b.x * v.x; in[4 * t + 1] = b.y * v.y;
-          in[4 * t + 2] = b.z * v.z; in[4 * t + 3] = b.w * v.w;
-        }
+    // row pass over every halo row of every plane of the chunk; the rounds
+    // that do not fill the block run tasks of XH / 2 outputs
+    {
+      const int T = P * HR * NSEG;
+      const int FULL = (T / NT) * NT;
+      auto tap = [&](int t) { return wh[t <= SB ? t : 2 * SB - t]; };
+      auto task_rows = [&](int task, int& q, int& r, int& seg) {
+        q = task / (HR * NSEG);
+        const int rem = task - q * (HR * NSEG);
+        r = rem / NSEG;
+        seg = rem - r * NSEG;
+      };
+      for (int task = tid; task < FULL; task += NT) {
+        int q, r, seg;
+        task_rows(task, q, r, seg);
+        const int qg = chunk * P + q;
+        if (qg > n) continue;
+        fir_row<SB, XH>(sB + r * LD + seg * XH, sF + (q * HR + r) * LD + seg * XH, qg == 0, tap,
+                        sH + (q * HR + r) * LDH + seg * XH);
       }
-      float h[XH];
-#pragma unroll
-      for (int o = 0; o < XH; ++o) h[o] = 0.0f;
-#pragma unroll
-      for (int t = 0; t < NTAP; ++t) {
-#pragma unroll
-        for (int o = 0; o < XH; ++o) h[o] = fmaf(wh[t <= SB ? t : 2 * SB - t], in[o + t], h[o]);
+      for (int hk = tid; hk < 2 * (T - FULL); hk += NT) {
+        int q, r, seg;
+        task_rows(FULL + (hk >> 1), q, r, seg);
+        const int qg = chunk * P + q;
+        if (qg > n) continue;
+        const int x = seg * XH + (hk & 1) * (XH / 2);
+        fir_row<SB, XH / 2>(sB + r * LD + x, sF + (q * HR + r) * LD + x, qg == 0, tap,
+                            sH + (q * HR + r) * LDH + x);
       }
-      float4* ph = reinterpret_cast<float4*>(sH + (q * HR + r) * LDH + seg * XH);
-#pragma unroll
-      for (int o = 0; o < XH / 4; ++o)
-        ph[o] = make_float4(h[4 * o], h[4 * o + 1], h[4 * o + 2], h[4 * o + 3]);
     }
     __syncthreads();
     // column pass at the tile's pixels, accumulate c_k V

@@ -80,34 +80,47 @@ bwd_tile_kernel(const BwdArgs a, const Taps taps, const Taps taps2) {
   const int yv0 = ((tid / TX) % (TY / YV)) * YV;
   const int gx = x0 + xv;
   const float* S1 = MODE == MODE_GAMMA ? a.B : a.C;   // the per-k plane multiplying sF
+  const int lane = tid & 31, warp = tid >> 5;
+  constexpr int CPL = (HC + 31) / 32;   // halo columns per lane
+  unsigned col_ok = 0;                  // bit j: column lane + 32 j inside the image
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) {
+    const int c = lane + 32 * j, xx = x0 - SB + c;
+    if (c < HC && xx >= 0 && xx < W) col_ok |= 1u << j;
+  }
   double sig = 0.0;                                   // GAMMA: log sigma_s partial
 
   for (int chunk = 0; chunk < nchunks; ++chunk) {
     const int qgv = chunk * P + qv;
-    // ---- stage the chunk's planes (image channels, or lambda planes)
-    for (int idx = tid; idx < P * HR * HC; idx += NT) {
-      const int q = idx / (HR * HC), r = (idx / HC) % HR, c = idx % HC;
-      const int qg = chunk * P + q;
-      const int yy = y0 - SB + r, xx = x0 - SB + c;
-      bool ok = yy >= 0 && yy < H && xx >= 0 && xx < W && qg <= n;
-      const float* src;
-      if (MODE == MODE_GAMMA) {
-        ok = ok && qg >= 1;
-        src = ok ? a.f + (size_t)(qg - 1) * N + (size_t)yy * W + xx : a.f;
-      } else {
-        src = ok ? a.lam + (size_t)qg * N + (size_t)yy * W + xx : a.lam;
-      }
-      cp_async4(sF + (q * HR + r) * LD + c, src, ok);
-    }
-    auto stage = [&](int k, float* dst) {
-      const float* Pk = S1 + (size_t)k * N;
-      for (int idx = tid; idx < HR * HC; idx += NT) {
-        const int r = idx / HC, c = idx % HC;
-        const int yy = y0 - SB + r, xx = x0 - SB + c;
-        const bool ok = yy >= 0 && yy < H && xx >= 0 && xx < W;
-        cp_async4(dst + r * LD + c, ok ? Pk + (size_t)yy * W + xx : Pk, ok);
+    // ---- stage the chunk's planes (image channels, or lambda planes) and the
+    // per-k plane: a warp copies whole halo rows, lanes over the columns
+    auto stage_rows = [&](const float* plane, float* dst) {
+      for (int r = warp; r < HR; r += NT / 32) {
+        const int yy = y0 - SB + r;
+        const bool rok = yy >= 0 && yy < H;
+        const float* grow = plane + (ptrdiff_t)yy * W + (x0 - SB);
+        float* srow = dst + r * LD;
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) {
+          const int c = lane + 32 * j;
+          if (c < HC) {
+            const bool ok = rok && ((col_ok >> j) & 1u);
+            cp_async4(srow + c, ok ? grow + c : plane, ok);
+          }
+        }
       }
     };
+    for (int q = 0; q < P; ++q) {
+      const int qg = chunk * P + q;
+      const bool have = MODE == MODE_GAMMA ? (qg >= 1 && qg <= n) : qg <= n;
+      if (have) {
+        stage_rows(MODE == MODE_GAMMA ? a.f + (size_t)(qg - 1) * N : a.lam + (size_t)qg * N,
+                   sF + q * HR * LD);
+      } else {
+        for (int i = tid; i < HR * LD; i += NT) sF[q * HR * LD + i] = 0.0f;
+      }
+    }
+    auto stage = [&](int k, float* dst) { stage_rows(S1 + (size_t)k * N, dst); };
     stage(0, sB0);
     cp_async_commit();
     // own-pixel values of this thread's plane

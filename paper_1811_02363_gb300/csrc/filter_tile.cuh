@@ -75,9 +75,10 @@ struct TileCfg {
 
 // XW outputs of the row FIR omega_1 (*) u on one halo row, u = b (plane 0)
 // or b f (the other planes), from 16-byte-aligned shared rows; results to out.
-template <int SB, int XW>
+// tap(t) is the weight of tap t (0 <= t <= 2 SB).
+template <int SB, int XW, class Wt>
 __device__ __forceinline__ void fir_row(const float* __restrict__ brow, const float* __restrict__ frow,
-                                        bool plane0, const Taps& taps, float* __restrict__ out) {
+                                        bool plane0, const Wt& tap, float* __restrict__ out) {
   constexpr int NIN4 = (XW + 2 * SB + 3) / 4, NTAP = 2 * SB + 1;
   const float4* pb = reinterpret_cast<const float4*>(brow);
   const float4* pf = reinterpret_cast<const float4*>(frow);
@@ -99,7 +100,7 @@ __device__ __forceinline__ void fir_row(const float* __restrict__ brow, const fl
 #pragma unroll
   for (int t = 0; t < NTAP; ++t) {
 #pragma unroll
-    for (int o = 0; o < XW; ++o) h[o] = fmaf(taps.w[t], in[o + t], h[o]);
+    for (int o = 0; o < XW; ++o) h[o] = fmaf(tap(t), in[o + t], h[o]);
   }
   float4* ph = reinterpret_cast<float4*>(out);
 #pragma unroll
@@ -211,12 +212,13 @@ filter_tile_kernel(const FilterArgs a, const Taps taps) {
         r = rem / NSEG;
         seg = rem - r * NSEG;
       };
+      auto tap = [&](int t) { return taps.w[t]; };
       for (int task = tid; task < FULL; task += NT) {
         int q, r, seg;
         task_rows(task, q, r, seg);
         const int qg = chunk * P + q;
         if (qg > n) continue;
-        fir_row<SB, XH>(sB + r * LD + seg * XH, sF + (q * HR + r) * LD + seg * XH, qg == 0, taps,
+        fir_row<SB, XH>(sB + r * LD + seg * XH, sF + (q * HR + r) * LD + seg * XH, qg == 0, tap,
                         sH + (q * HR + r) * LDH + seg * XH);
       }
       for (int hk = tid; hk < 2 * (T - FULL); hk += NT) {
@@ -225,7 +227,7 @@ filter_tile_kernel(const FilterArgs a, const Taps taps) {
         const int qg = chunk * P + q;
         if (qg > n) continue;
         const int x = seg * XH + (hk & 1) * (XH / 2);
-        fir_row<SB, XH / 2>(sB + r * LD + x, sF + (q * HR + r) * LD + x, qg == 0, taps,
+        fir_row<SB, XH / 2>(sB + r * LD + x, sF + (q * HR + r) * LD + x, qg == 0, tap,
                             sH + (q * HR + r) * LDH + x);
       }
     }

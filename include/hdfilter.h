@@ -227,11 +227,14 @@ enum {
 };
 
 typedef struct {
-  int SB;        /* compiled window bucket (half-width >= S) */
-  int planes;    /* n + 1 planes per centre */
-  int P, TY;     /* planes per work item, tile height (tile width 32) */
-  float ms;      /* best time of the persistent launch over the images of this key */
-  int chosen;    /* 1 for the shape kept */
+  int SB;        /* compiled window bucket (half-width >= S); 0 marks a clustering-plan trial */
+  int planes;    /* n + 1 planes per centre; for SB == 0 the number of clustering groups
+                    (0: one group per image) */
+  int P, TY;     /* planes per work item, tile height (tile width 32); for SB == 0, P is the
+                    blocks per group (0: sized per image) and TY is 0 */
+  float ms;      /* best time of the persistent launch over the images of this key (for
+                    SB == 0: the clustering launch of the whole batch) */
+  int chosen;    /* 1 for the shape (plan) kept */
 } hdf_tile_trial;
 
 typedef struct {
@@ -247,8 +250,11 @@ typedef struct {
 } hdf_batch_info;
 
 /* Validate `count` descriptors (S filled in when 0), plan the clustering
- * groups and the default tile shapes, and allocate every workspace in one
- * device arena.  descs[i].guide_dtype selects the guide storage of image i:
+ * groups (one block group per image while each gets at least 19 blocks,
+ * else four equal groups that take their images in turn; hdf_batch_tune
+ * times the alternatives) and the default tile shapes, and allocate every
+ * workspace in one device arena.  descs[i].guide_dtype selects the guide
+ * storage of image i:
  * with HDF_GUIDE_BF16 and a NULL guide at bind time, the run converts the
  * image into a bfloat16 guide it owns (guide = image, rho == n).
  * Synchronous; the only batch call that allocates device memory. */
@@ -276,7 +282,10 @@ hdf_status hdf_batch_set_centers(hdf_batch* b, int i, const float* h_mu, int K);
  * gave up) are recorded per image: hdf_batch_get_stats. */
 hdf_status hdf_batch_run(hdf_batch* b, int flags, void* stream);
 
-/* Autotuner: run the batch once, then for every (window bucket, plane count)
+/* Autotuner: run the batch once; time the clustering launch of the batch
+ * under each clustering plan (one block group per image sized by its work,
+ * or M = 1, 2, 4, ... equal groups that take their images one after the
+ * other) and keep the fastest; then for every (window bucket, plane count)
  * present time each compiled tile shape that fits in shared memory on the
  * persistent launch restricted to those images (best of `reps` runs, CUDA
  * events) and keep the fastest.  Synchronous; drops a captured graph. */

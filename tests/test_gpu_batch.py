@@ -175,6 +175,33 @@ def test_batch_clustering_matches_oracle(api):
         assert abs(st["cluster_error"] - oek) <= 1e-6 * oek, (i, st["cluster_error"], oek)
 
 
+def test_tuned_clustering_plan_matches_oracle(api):
+    """The tuner times the clustering launch under every plan (a group per
+    image, or M equal groups taking their images in turn), keeps one, and the
+    batch run under the kept plan still matches the oracle's clustering."""
+    images = _images([
+        (lambda: synthetic.color_rectangles(96, 80, seed=81), 3.0, 0.2, 8),
+        (lambda: synthetic.hyperspectral_mixture(64, 64, 16, seed=82), 2.0, 0.2, 16),
+        (lambda: synthetic.color_rectangles(150, 97, seed=83), 5.0, 0.25, 32),
+        (lambda: synthetic.hyperspectral_mixture(70, 50, 16, seed=84), 6.0, 0.3, 8),
+        (lambda: synthetic.color_rectangles(40, 33, seed=85), 2.0, 0.2, 4),
+    ])
+    b, fs, gs = _bound_batch(api, images)
+    trials = [t for t in b.tune(reps=1) if t["SB"] == 0]
+    assert [t["planes"] for t in trials] == [0, 1, 2, 4]
+    assert sum(t["chosen"] for t in trials) == 1 and all(t["ms"] > 0 for t in trials)
+    b.run(graph=True)
+    torch.cuda.synchronize()
+    for i, (f, ss, sr, K) in enumerate(images):
+        omu, _, sse = O.bisecting_kmeans(f.reshape(f.shape[0], -1).T.astype(np.float64), K)
+        st = b.stats(i)
+        mu = b.get_centers(i)
+        assert st["device_error"] == 0 and st["K_eff"] == omu.shape[0], (i, st)
+        assert np.max(np.abs(mu - omu)) <= 1e-5 * max(np.abs(omu).max(), 1e-30), i
+        oek = float(sse.sum())
+        assert abs(st["cluster_error"] - oek) <= 1e-6 * oek, (i, st["cluster_error"], oek)
+
+
 def test_more_images_than_sms(api):
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     count = sms + 9
@@ -187,7 +214,8 @@ def test_more_images_than_sms(api):
     b.run(graph=True)
     torch.cuda.synchronize()
     info = b.info()
-    assert info["ngroups"] == sms and info["grid_cluster"] == sms
+    # more images than 8: four equal block groups, each taking its images in turn
+    assert info["ngroups"] == 4 and info["grid_cluster"] == 4 * (sms // 4)
     mus = [_centres(f, K) for f, _, _, K in images]
     for i in range(count):
         mu = b.get_centers(i)

@@ -41,13 +41,29 @@ def window_halfwidth(sigma_s: float) -> int:
     return int(math.ceil(3.0 * sigma_s))
 
 
-def spatial_weights_1d(sigma_s: float, S: int) -> np.ndarray:
+def spatial_weights_1d(sigma_s: float, S: int, spatial: str = "gauss") -> np.ndarray:
     """omega_1(t) = exp(-t^2 / 2 sigma_s^2) for t = -S..S.  The 2-D spatial
     kernel of Sec. III, omega(j) = exp(-|j|^2 / 2 sigma_s^2), is the outer
     product omega_1(j_1) omega_1(j_2) (unnormalised: the scale cancels in
-    Eq. (1)-(2))."""
+    Eq. (1)-(2)).  ``spatial='box'``: the box kernel Sec. III uses for
+    nonlocal means, omega = 1 on W, i.e. omega_1 = 1 (sigma_s unused)."""
     t = np.arange(-S, S + 1, dtype=np.float64)
+    if spatial == "box":
+        return np.ones_like(t)
+    if spatial != "gauss":
+        raise ValueError(spatial)
     return np.exp(-(t * t) / (2.0 * sigma_s * sigma_s))
+
+
+def spatial_weight(j1, j2, sigma_s: float, spatial: str = "gauss"):
+    """omega(j) at offsets j = (j1, j2) inside W: the Gaussian of Sec. III or
+    1 for the box kernel (arrays broadcast)."""
+    if spatial == "box":
+        return np.ones(np.broadcast(j1, j2).shape) if np.ndim(j1) or np.ndim(j2) else 1.0
+    if spatial != "gauss":
+        raise ValueError(spatial)
+    return np.exp(-(np.asarray(j1, dtype=np.float64) ** 2 + np.asarray(j2, dtype=np.float64) ** 2)
+                  / (2.0 * sigma_s * sigma_s))
 
 
 def range_kernel(sq_dist: np.ndarray, sigma_r: float) -> np.ndarray:
@@ -60,7 +76,7 @@ def range_kernel(sq_dist: np.ndarray, sigma_r: float) -> np.ndarray:
 # --------------------------------------------------------------------------
 
 def bruteforce(f: np.ndarray, p: np.ndarray, sigma_s: float, sigma_r: float,
-               S: int) -> np.ndarray:
+               S: int, spatial: str = "gauss") -> np.ndarray:
     """g(i) = sum_{j in W} omega(j) phi(p(i-j) - p(i)) f(i-j) / eta(i), with
     eta(i) the same sum without f (Eq. (1), Eq. (2)); W = [-S, S]^2.
 
@@ -75,7 +91,7 @@ def bruteforce(f: np.ndarray, p: np.ndarray, sigma_s: float, sigma_r: float,
     den = np.zeros((H, W))
     for j1 in range(-S, S + 1):
         for j2 in range(-S, S + 1):
-            w = math.exp(-(j1 * j1 + j2 * j2) / (2.0 * sigma_s * sigma_s))
+            w = float(spatial_weight(j1, j2, sigma_s, spatial))
             # pixels i = (y, x) whose neighbour i - j = (y - j1, x - j2) is inside
             y0, y1 = max(0, j1), min(H, H + j1)
             x0, x1 = max(0, j2), min(W, W + j2)
@@ -90,7 +106,7 @@ def bruteforce(f: np.ndarray, p: np.ndarray, sigma_s: float, sigma_r: float,
 
 
 def bruteforce_at(f: np.ndarray, p: np.ndarray, sigma_s: float, sigma_r: float,
-                  S: int, pixels: np.ndarray) -> np.ndarray:
+                  S: int, pixels: np.ndarray, spatial: str = "gauss") -> np.ndarray:
     """Eq. (1)-(2) evaluated at the listed pixels only (rows of (y, x)), one
     pixel at a time by a direct sum over its window.  Returns (len, n)."""
     f = np.asarray(f, dtype=np.float64)
@@ -102,7 +118,7 @@ def bruteforce_at(f: np.ndarray, p: np.ndarray, sigma_s: float, sigma_r: float,
         xa, xb = max(0, x - S), min(W, x + S + 1)
         dy = (y - np.arange(ya, yb, dtype=np.float64))[:, None]
         dx = (x - np.arange(xa, xb, dtype=np.float64))[None, :]
-        w = np.exp(-(dy * dy + dx * dx) / (2.0 * sigma_s * sigma_s))
+        w = spatial_weight(dy, dx, sigma_s, spatial)
         d2 = ((p[:, ya:yb, xa:xb] - p[:, y:y + 1, x:x + 1]) ** 2).sum(axis=0)
         wt = w * range_kernel(d2, sigma_r)
         out[m] = (wt * f[:, ya:yb, xa:xb]).sum(axis=(1, 2)) / wt.sum()
@@ -261,23 +277,24 @@ def conv_cols(x: np.ndarray, w1: np.ndarray) -> np.ndarray:
     return np.swapaxes(conv_rows(np.swapaxes(x, -1, -2), w1), -1, -2)
 
 
-def spatial_conv(x: np.ndarray, sigma_s: float, S: int) -> np.ndarray:
+def spatial_conv(x: np.ndarray, sigma_s: float, S: int, spatial: str = "gauss") -> np.ndarray:
     """(omega * x)(i) = sum_{j in W} omega(j) x(i - j) over the window
     W = [-S, S]^2, zero extension outside the image.  omega factorises, so
     the 2-D sum is done as a row pass followed by a column pass; the tests
     pin this against the direct 2-D sum."""
-    w1 = spatial_weights_1d(sigma_s, S)
+    w1 = spatial_weights_1d(sigma_s, S, spatial)
     return conv_cols(conv_rows(np.asarray(x, dtype=np.float64), w1), w1)
 
 
-def spatial_conv_direct(x: np.ndarray, sigma_s: float, S: int) -> np.ndarray:
+def spatial_conv_direct(x: np.ndarray, sigma_s: float, S: int,
+                        spatial: str = "gauss") -> np.ndarray:
     """Direct 2-D form of ``spatial_conv`` (small inputs)."""
     x = np.asarray(x, dtype=np.float64)
     H, Wd = x.shape[-2:]
     out = np.zeros_like(x)
     for j1 in range(-S, S + 1):
         for j2 in range(-S, S + 1):
-            w = math.exp(-(j1 * j1 + j2 * j2) / (2.0 * sigma_s * sigma_s))
+            w = float(spatial_weight(j1, j2, sigma_s, spatial))
             y0, y1 = max(0, j1), min(H, H + j1)
             x0, x1 = max(0, j2), min(Wd, Wd + j2)
             if y0 < y1 and x0 < x1:
@@ -291,7 +308,7 @@ def spatial_conv_direct(x: np.ndarray, sigma_s: float, S: int) -> np.ndarray:
 
 def fast_filter(f: np.ndarray, p: np.ndarray, mu: np.ndarray, sigma_s: float,
                 sigma_r: float, S: int, variant: str = "opt",
-                guard: bool = True, return_stats: bool = False):
+                guard: bool = True, return_stats: bool = False, spatial: str = "gauss"):
     """Algorithm 1 with given centres mu (K, rho):
 
       A (Eq. (12)) and its pseudo-inverse;
@@ -306,6 +323,8 @@ def fast_filter(f: np.ndarray, p: np.ndarray, mu: np.ndarray, sigma_s: float,
     the pixel falls back to the indicator value v_s(i)/r_s(i) (Eq. (18)) with s
     the nearest centre, and to f(i) if r_s(i) is 0 as well.
 
+    ``spatial``: 'gauss' (Sec. III's Gaussian omega) or 'box' (omega = 1 on
+    W, Sec. III's kernel for nonlocal means).
     Returns g_hat (n, H, W) [, dict(fallback=count)]."""
     f = np.asarray(f, dtype=np.float64)
     p = np.asarray(p, dtype=np.float64)
@@ -328,8 +347,8 @@ def fast_filter(f: np.ndarray, p: np.ndarray, mu: np.ndarray, sigma_s: float,
     v_s = np.zeros((n, H, W))
     r_s = np.zeros((H, W))
     for k in range(K):
-        vk = spatial_conv(B[k][None] * f, sigma_s, S)               # omega * u_k
-        rk = spatial_conv(B[k], sigma_s, S)                         # omega * b_k
+        vk = spatial_conv(B[k][None] * f, sigma_s, S, spatial)      # omega * u_k
+        rk = spatial_conv(B[k], sigma_s, S, spatial)                # omega * b_k
         v += C[k] * vk
         r += C[k] * rk
         np.maximum(r_max, rk, out=r_max)
@@ -348,7 +367,8 @@ def fast_filter(f: np.ndarray, p: np.ndarray, mu: np.ndarray, sigma_s: float,
 
 
 def fast_filter_at(f: np.ndarray, p: np.ndarray, mu: np.ndarray, sigma_s: float,
-                   sigma_r: float, S: int, pixels: np.ndarray) -> np.ndarray:
+                   sigma_r: float, S: int, pixels: np.ndarray,
+                   spatial: str = "gauss") -> np.ndarray:
     """Eq. (15)-(16) at the listed pixels only, with v_k(i) and r_k(i) taken
     straight from their definitions Eq. (13)-(14) as sums over the window
     (one pixel at a time).  Same guard as ``fast_filter``.  Returns (len, n)."""
@@ -363,7 +383,7 @@ def fast_filter_at(f: np.ndarray, p: np.ndarray, mu: np.ndarray, sigma_s: float,
         xa, xb = max(0, x - S), min(W, x + S + 1)
         dy = (y - np.arange(ya, yb, dtype=np.float64))[:, None]
         dx = (x - np.arange(xa, xb, dtype=np.float64))[None, :]
-        w = np.exp(-(dy * dy + dx * dx) / (2.0 * sigma_s * sigma_s))
+        w = spatial_weight(dy, dx, sigma_s, spatial)
         pw = p[:, ya:yb, xa:xb]
         d2w = ((pw[None] - mu[:, :, None, None]) ** 2).sum(axis=1)   # (K, h, w)
         phi = range_kernel(d2w, sigma_r)

@@ -58,6 +58,9 @@ typedef enum {
 enum { HDF_GUIDE_F32 = 0, HDF_GUIDE_BF16 = 1 };
 enum { HDF_COEF_OPT = 0,        /* c(i) = A^+ b(i), Eq. (11) */
        HDF_COEF_INDICATOR = 1   /* c(i) = e_s, s the nearest centre, Eq. (17) */ };
+enum { HDF_SPATIAL_GAUSS = 0,   /* omega(j) = exp(-|j|^2 / 2 sigma_s^2) on W (Sec. III) */
+       HDF_SPATIAL_BOX = 1      /* omega(j) = 1 on W, the kernel Sec. III uses for nonlocal
+                                   means; sigma_s only sets S when S = 0 */ };
 
 /* Limits of this build. */
 #define HDF_MAX_K 64           /* clusters */
@@ -75,6 +78,7 @@ typedef struct {
   double sigma_r;    /* range Gaussian std (guide units), > 0 */
   int guide_dtype;   /* HDF_GUIDE_F32 or HDF_GUIDE_BF16 */
   int coef;          /* HDF_COEF_OPT or HDF_COEF_INDICATOR */
+  int spatial;       /* HDF_SPATIAL_GAUSS or HDF_SPATIAL_BOX */
 } hdf_desc;
 
 typedef struct hdf_handle hdf_handle;
@@ -142,9 +146,10 @@ hdf_status hdf_apply(hdf_handle* h, const float* d_f, const void* d_p, float* d_
  *   d_grad_f          (n, H, W): dL/df; when d_p == d_f (guide = image) it
  *                     includes the path through b_k(p) and c(p);
  *   d_grad_log_sigma  2 float64: dL/dlog sigma_s, dL/dlog sigma_r.
- * Convolution outputs are recomputed, not stored.  Requires HDF_COEF_OPT and
- * an A that is full rank under the pinv tolerance (dA^+ of a truncated
- * pseudo-inverse is not defined): HDF_EDOMAIN is recorded otherwise.
+ * Convolution outputs are recomputed, not stored.  Requires HDF_COEF_OPT,
+ * the Gaussian spatial kernel (HDF_EUNSUPPORTED for the box: no sigma_s
+ * derivative) and an A that is full rank under the pinv tolerance (dA^+ of a
+ * truncated pseudo-inverse is not defined): HDF_EDOMAIN is recorded otherwise.
  * Asynchronous.  Differentiates Eq. (15)-(16); the paper has no backward pass. */
 hdf_status hdf_backward(hdf_handle* h, const float* d_f, const void* d_p,
                         const float* d_grad_g, float* d_grad_f,

@@ -12,13 +12,15 @@ LIB_PATH = os.path.join(_HERE, "lib", "libhdfilter.so")
 HDF_OK, HDF_EINVAL, HDF_ENOMEM, HDF_ECUDA, HDF_ETIMEOUT, HDF_EDOMAIN, HDF_EUNSUPPORTED = range(7)
 HDF_GUIDE_F32, HDF_GUIDE_BF16 = 0, 1
 HDF_COEF_OPT, HDF_COEF_INDICATOR = 0, 1
+HDF_SPATIAL_GAUSS, HDF_SPATIAL_BOX = 0, 1
 HDF_MAX_K, HDF_MAX_RHO, HDF_MAX_S, HDF_MAX_N = 64, 64, 32, 256
 
 
 class hdf_desc(C.Structure):
     _fields_ = [("H", C.c_int), ("W", C.c_int), ("n", C.c_int), ("rho", C.c_int),
                 ("K", C.c_int), ("S", C.c_int), ("sigma_s", C.c_double),
-                ("sigma_r", C.c_double), ("guide_dtype", C.c_int), ("coef", C.c_int)]
+                ("sigma_r", C.c_double), ("guide_dtype", C.c_int), ("coef", C.c_int),
+                ("spatial", C.c_int)]
 
 
 class hdf_stats(C.Structure):

@@ -40,13 +40,15 @@ def window_halfwidth(sigma_s: float) -> int:
     return int(math.ceil(3.0 * sigma_s))
 
 
-def make_desc(H, W, n, rho, K, sigma_s, sigma_r, S=0, guide_dtype="f32", coef="opt") -> L.hdf_desc:
+def make_desc(H, W, n, rho, K, sigma_s, sigma_r, S=0, guide_dtype="f32", coef="opt",
+              spatial="gauss") -> L.hdf_desc:
     d = L.hdf_desc()
     d.H, d.W, d.n, d.rho, d.K = int(H), int(W), int(n), int(rho), int(K)
     d.S = int(S) if S else window_halfwidth(sigma_s)
     d.sigma_s, d.sigma_r = float(sigma_s), float(sigma_r)
     d.guide_dtype = {"f32": L.HDF_GUIDE_F32, "bf16": L.HDF_GUIDE_BF16}[guide_dtype]
     d.coef = {"opt": L.HDF_COEF_OPT, "indicator": L.HDF_COEF_INDICATOR}[coef]
+    d.spatial = {"gauss": L.HDF_SPATIAL_GAUSS, "box": L.HDF_SPATIAL_BOX}[spatial]
     return d
 
 
@@ -57,8 +59,9 @@ class HDFilter:
     device; ``set_centers(mu)`` installs given centres instead; ``apply(f, p)``
     filters; ``backward(...)`` returns gradients."""
 
-    def __init__(self, H, W, n, rho, K, sigma_s, sigma_r, S=0, guide_dtype="f32", coef="opt"):
-        self.desc = make_desc(H, W, n, rho, K, sigma_s, sigma_r, S, guide_dtype, coef)
+    def __init__(self, H, W, n, rho, K, sigma_s, sigma_r, S=0, guide_dtype="f32", coef="opt",
+                 spatial="gauss"):
+        self.desc = make_desc(H, W, n, rho, K, sigma_s, sigma_r, S, guide_dtype, coef, spatial)
         self._h = C.c_void_p()
         L.check(L.lib().hdf_create(C.byref(self._h), C.byref(self.desc)), "hdf_create")
         L.check(L.lib().hdf_get_desc(self._h, C.byref(self.desc)), "hdf_get_desc")
@@ -178,7 +181,7 @@ class HDFilter:
 
 
 def bruteforce(f: torch.Tensor, p: torch.Tensor | None, sigma_s: float, sigma_r: float,
-               S: int = 0, out: torch.Tensor | None = None) -> torch.Tensor:
+               S: int = 0, out: torch.Tensor | None = None, spatial: str = "gauss") -> torch.Tensor:
     """Eq. (1)-(2) by direct summation on the GPU."""
     _check_image(f, "f")
     p = f if p is None else p
@@ -188,7 +191,7 @@ def bruteforce(f: torch.Tensor, p: torch.Tensor | None, sigma_s: float, sigma_r:
         raise ValueError("p must be float32 or bfloat16")
     n, H, W = f.shape
     d = make_desc(H, W, n, p.shape[0], 1, sigma_s, sigma_r, S,
-                  "f32" if p.dtype == torch.float32 else "bf16")
+                  "f32" if p.dtype == torch.float32 else "bf16", spatial=spatial)
     g = torch.empty_like(f) if out is None else out
     _check_image(g, "out")
     L.check(L.lib().hdf_bruteforce(C.byref(d), _ptr(f), _ptr(p), _ptr(g), _stream()),
@@ -232,7 +235,8 @@ class Batch:
     combine tiles, CUDA-graph replay, and an autotuner for tile shapes.
 
     ``specs``: one dict per image with keys H, W, n, K, sigma_s, sigma_r and
-    optionally rho (default n), S, guide_dtype ("f32" / "bf16"), coef.
+    optionally rho (default n), S, guide_dtype ("f32" / "bf16"), coef, spatial
+    ("gauss" / "box").
     ``bind(fs, gs, ps=None)`` binds CUDA tensors (ps entries None = guide is
     the image; with guide_dtype "bf16" the run stores it as bfloat16)."""
 
@@ -242,7 +246,8 @@ class Batch:
         for i, s in enumerate(self.specs):
             descs[i] = make_desc(s["H"], s["W"], s["n"], s.get("rho", s["n"]), s["K"],
                                  s["sigma_s"], s["sigma_r"], s.get("S", 0),
-                                 s.get("guide_dtype", "f32"), s.get("coef", "opt"))
+                                 s.get("guide_dtype", "f32"), s.get("coef", "opt"),
+                                 s.get("spatial", "gauss"))
         self.descs = descs
         self._b = C.c_void_p()
         L.check(L.lib().hdf_batch_create(C.byref(self._b), len(specs), descs), "hdf_batch_create")

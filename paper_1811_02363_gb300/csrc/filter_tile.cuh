@@ -33,6 +33,7 @@ struct FilterArgs {
   float* rmax;          // (H, W) max_k r_k
   const int* ctrl;
   int H, W, n;
+  int box, S;           // box spatial kernel (omega = 1 on W) of half-width S <= SB
 };
 
 __device__ __forceinline__ void cp_async4(float* smem, const float* gmem, bool valid) {
@@ -107,7 +108,64 @@ __device__ __forceinline__ void fir_row(const float* __restrict__ brow, const fl
   for (int o = 0; o < XW / 4; ++o) ph[o] = make_float4(h[4 * o], h[4 * o + 1], h[4 * o + 2], h[4 * o + 3]);
 }
 
-template <int SB, int P, int TY>
+// Largest D = SB - S of a call whose half-width S falls in bucket SB (the
+// buckets are 3, 6, 9, 12, 15, 18, 24, 32).
+__host__ __device__ constexpr int box_dmax(int SB) { return SB <= 18 ? 2 : (SB <= 24 ? 5 : 7); }
+
+// Box window sums over a register array: out[o] = sum of in[o + t] for
+// t = d .. 2 SB - d (the box kernel of half-width S = SB - d), o < NO, with d
+// in 0 .. box_dmax(SB) known only at run time.  Prefix sums P[m] = in[0] +
+// ... + in[m - 1] make every window one difference, P[o + 2 SB + 1 - d] -
+// P[o + d]; the candidates for each d have compile-time indices and the
+// uniform d selects one, so nothing is indexed at run time.  O(1) per output;
+// the differences of prefix sums carry about as much rounding as a FIR.
+template <int SB, int NO, int NI>
+__device__ __forceinline__ void box_sums(int d, const float (&in)[NI], float (&out)[NO]) {
+  constexpr int DM = box_dmax(SB);
+  constexpr int NP = NO + 2 * SB + 1;   // prefix sums needed: P[0 .. NO + 2 SB]
+  static_assert(NP - 1 <= NI, "window inputs");
+  float P[NP];
+  P[0] = 0.0f;
+#pragma unroll
+  for (int m = 1; m < NP; ++m) P[m] = P[m - 1] + in[m - 1];
+#pragma unroll
+  for (int o = 0; o < NO; ++o) {
+    float r = P[o + 2 * SB + 1] - P[o];
+#pragma unroll
+    for (int D = 1; D <= DM; ++D)
+      if (d == D) r = P[o + 2 * SB + 1 - D] - P[o + D];
+    out[o] = r;
+  }
+}
+
+// The box kernel's row pass (omega_1 = 1 on [-S, S]): the inputs are loaded
+// as in fir_row, the XW outputs are running window sums.
+template <int SB, int XW>
+__device__ __forceinline__ void box_row(const float* __restrict__ brow, const float* __restrict__ frow,
+                                        bool plane0, int S, float* __restrict__ out) {
+  constexpr int NIN4 = (XW + 2 * SB + 3) / 4;
+  const float4* pb = reinterpret_cast<const float4*>(brow);
+  const float4* pf = reinterpret_cast<const float4*>(frow);
+  float in[4 * NIN4];
+#pragma unroll
+  for (int t = 0; t < NIN4; ++t) {
+    const float4 b = pb[t];
+    if (plane0) {
+      in[4 * t] = b.x; in[4 * t + 1] = b.y; in[4 * t + 2] = b.z; in[4 * t + 3] = b.w;
+    } else {
+      const float4 v = pf[t];
+      in[4 * t] = b.x * v.x; in[4 * t + 1] = b.y * v.y;
+      in[4 * t + 2] = b.z * v.z; in[4 * t + 3] = b.w * v.w;
+    }
+  }
+  float h[XW];
+  box_sums<SB, XW, 4 * NIN4>(SB - S, in, h);
+  float4* ph = reinterpret_cast<float4*>(out);
+#pragma unroll
+  for (int o = 0; o < XW / 4; ++o) ph[o] = make_float4(h[4 * o], h[4 * o + 1], h[4 * o + 2], h[4 * o + 3]);
+}
+
+template <int SB, int P, int TY, bool BOX>
 __global__ void __launch_bounds__(512, 1)
 filter_tile_kernel(const FilterArgs a, const Taps taps) {
   using Cfg = TileCfg<SB, P, TY>;
@@ -218,8 +276,12 @@ filter_tile_kernel(const FilterArgs a, const Taps taps) {
         task_rows(task, q, r, seg);
         const int qg = chunk * P + q;
         if (qg > n) continue;
-        fir_row<SB, XH>(sB + r * LD + seg * XH, sF + (q * HR + r) * LD + seg * XH, qg == 0, tap,
-                        sH + (q * HR + r) * LDH + seg * XH);
+        if constexpr (BOX)
+          box_row<SB, XH>(sB + r * LD + seg * XH, sF + (q * HR + r) * LD + seg * XH, qg == 0, a.S,
+                          sH + (q * HR + r) * LDH + seg * XH);
+        else
+          fir_row<SB, XH>(sB + r * LD + seg * XH, sF + (q * HR + r) * LD + seg * XH, qg == 0, tap,
+                          sH + (q * HR + r) * LDH + seg * XH);
       }
       for (int hk = tid; hk < 2 * (T - FULL); hk += NT) {
         int q, r, seg;
@@ -227,24 +289,32 @@ filter_tile_kernel(const FilterArgs a, const Taps taps) {
         const int qg = chunk * P + q;
         if (qg > n) continue;
         const int x = seg * XH + (hk & 1) * (XH / 2);
-        fir_row<SB, XH / 2>(sB + r * LD + x, sF + (q * HR + r) * LD + x, qg == 0, tap,
-                            sH + (q * HR + r) * LDH + x);
+        if constexpr (BOX)
+          box_row<SB, XH / 2>(sB + r * LD + x, sF + (q * HR + r) * LD + x, qg == 0, a.S,
+                              sH + (q * HR + r) * LDH + x);
+        else
+          fir_row<SB, XH / 2>(sB + r * LD + x, sF + (q * HR + r) * LD + x, qg == 0, tap,
+                              sH + (q * HR + r) * LDH + x);
       }
     }
     __syncthreads();
     // ---- column pass at the tile's pixels, accumulate c_k V
     if (qgv <= n) {
-      float in[YV + 2 * SB];
       const float* ph = sH + (qv * HR + yv0) * LDH + xv;
+      float v[YV];
+      float in[YV + 2 * SB];
 #pragma unroll
       for (int t = 0; t < YV + 2 * SB; ++t) in[t] = ph[t * LDH];
-      float v[YV];
+      if constexpr (BOX) {   // column window sums of the box kernel
+        box_sums<SB, YV, YV + 2 * SB>(SB - a.S, in, v);
+      } else {
 #pragma unroll
-      for (int o = 0; o < YV; ++o) v[o] = 0.0f;
+        for (int o = 0; o < YV; ++o) v[o] = 0.0f;
 #pragma unroll
-      for (int t = 0; t < NTAP; ++t) {
+        for (int t = 0; t < NTAP; ++t) {
 #pragma unroll
-        for (int o = 0; o < YV; ++o) v[o] = fmaf(taps.w[t], in[o + t], v[o]);
+          for (int o = 0; o < YV; ++o) v[o] = fmaf(taps.w[t], in[o + t], v[o]);
+        }
       }
 #pragma unroll
       for (int o = 0; o < YV; ++o) acc[o] = fmaf(ccur[o], v[o], acc[o]);
@@ -275,17 +345,24 @@ filter_tile_kernel(const FilterArgs a, const Taps taps) {
   }
 }
 
-template <int SB, int P, int TY>
-cudaError_t launch_filter_tile(const FilterArgs& a, const Taps& taps, cudaStream_t st) {
+template <int SB, int P, int TY, bool BOX>
+cudaError_t launch_filter_tile_k(const FilterArgs& a, const Taps& taps, cudaStream_t st) {
   using Cfg = TileCfg<SB, P, TY>;
-  cudaError_t e = cudaFuncSetAttribute(filter_tile_kernel<SB, P, TY>,
+  cudaError_t e = cudaFuncSetAttribute(filter_tile_kernel<SB, P, TY, BOX>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)Cfg::SMEM);
   if (e != cudaSuccess) return e;
   const int nchunks = (a.n + 1 + P - 1) / P;
   dim3 grid((a.W + Cfg::TX - 1) / Cfg::TX, (a.H + TY - 1) / TY, nchunks);
-  filter_tile_kernel<SB, P, TY><<<grid, Cfg::NT, Cfg::SMEM, st>>>(a, taps);
+  filter_tile_kernel<SB, P, TY, BOX><<<grid, Cfg::NT, Cfg::SMEM, st>>>(a, taps);
   return cudaGetLastError();
+}
+
+// The Gaussian (taps) or the box (running sums) instantiation.
+template <int SB, int P, int TY>
+cudaError_t launch_filter_tile(const FilterArgs& a, const Taps& taps, cudaStream_t st) {
+  return a.box ? launch_filter_tile_k<SB, P, TY, true>(a, taps, st)
+               : launch_filter_tile_k<SB, P, TY, false>(a, taps, st);
 }
 
 // Dispatch entry point over the compiled (SB, P, TY) instantiations.

@@ -30,6 +30,7 @@ hdf_status check_desc(hdf_desc* d) {
   if (d->S == 0) d->S = (int)ceil(3.0 * d->sigma_s);
   if (d->guide_dtype != HDF_GUIDE_F32 && d->guide_dtype != HDF_GUIDE_BF16) return HDF_EINVAL;
   if (d->coef != HDF_COEF_OPT && d->coef != HDF_COEF_INDICATOR) return HDF_EINVAL;
+  if (d->spatial != HDF_SPATIAL_GAUSS && d->spatial != HDF_SPATIAL_BOX) return HDF_EINVAL;
   if (d->K > HDF_MAX_K || d->rho > HDF_MAX_RHO || d->S > HDF_MAX_S || d->n > HDF_MAX_N)
     return HDF_EUNSUPPORTED;
   if ((long long)d->H * d->W >= (1LL << 31)) return HDF_EUNSUPPORTED;
@@ -52,10 +53,12 @@ cudaError_t dalloc(T** p, size_t count) {
 
 namespace hdf {
 
-Taps make_taps(double sigma_s, int S) {
+Taps make_taps(double sigma_s, int S, int spatial) {
   Taps t;
   memset(&t, 0, sizeof(t));
-  for (int j = -S; j <= S; ++j) t.w[j + S] = (float)exp(-(double)(j * j) / (2.0 * sigma_s * sigma_s));
+  for (int j = -S; j <= S; ++j)
+    t.w[j + S] = spatial == HDF_SPATIAL_BOX ? 1.0f
+                                            : (float)exp(-(double)(j * j) / (2.0 * sigma_s * sigma_s));
   return t;
 }
 
@@ -230,7 +233,7 @@ hdf_status hdf_apply(hdf_handle* h, const float* d_f, const void* d_p, float* d_
 hdf_status hdf_backward(hdf_handle* h, const float* d_f, const void* d_p, const float* d_grad_g,
                         float* d_grad_f, double* d_grad_log_sigma, void* stream) {
   if (!h || !d_f || !d_p || !d_grad_g || !d_grad_f || !d_grad_log_sigma) return HDF_EINVAL;
-  if (h->d.coef != HDF_COEF_OPT) return HDF_EUNSUPPORTED;
+  if (h->d.coef != HDF_COEF_OPT || h->d.spatial != HDF_SPATIAL_GAUSS) return HDF_EUNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   HDF_CUDA(hdf::launch_backward(h, d_f, d_p, d_grad_g, d_grad_f, d_grad_log_sigma, st),
            "backward");

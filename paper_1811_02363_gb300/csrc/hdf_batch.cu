@@ -271,7 +271,7 @@ BatchImg make_img(const Img& m) {
   r.SB = m.SB;
   r.P = m.P;
   r.TY = m.TY;
-  const Taps t = make_taps(m.d.sigma_s, m.d.S);
+  const Taps t = make_taps(m.d.sigma_s, m.d.S, m.d.spatial);
   for (int j = -m.d.S; j <= m.d.S; ++j) r.taps[m.SB + j] = t.w[m.d.S + j];
   return r;
 }

@@ -111,7 +111,7 @@ cudaError_t launch_backward(hdf_handle* h, const float* f, const void* p, const 
                             float* grad_f, double* grad_ls, cudaStream_t st);
 
 // Host helpers.
-Taps make_taps(double sigma_s, int S);
+Taps make_taps(double sigma_s, int S, int spatial);   // omega_1 at [t + S], 0 beyond S
 hdf_status cuda_fail(cudaError_t e, const char* where);   // records the text for hdf_last_cuda_error
 hdf_status check_desc(hdf_desc* d);                       // validates, fills S = ceil(3 sigma_s) if 0
 int filter_bucket(int S);                                 // compiled window bucket >= S, -1 if none

@@ -230,7 +230,7 @@ cudaError_t launch_backward(hdf_handle* h, const float* f, const void* p, const 
   if ((e = launch_filter(h, f, h->bw_g, st)) != cudaSuccess) return e;
   // 2. guarded pixels
   if ((e = cudaMemsetAsync(h->bw_flag, 0, h->N, st)) != cudaSuccess) return e;
-  const Taps exact = make_taps(d.sigma_s, d.S);
+  const Taps exact = make_taps(d.sigma_s, d.S, d.spatial);
   bwd_fallback_kernel<<<sms, 256, 0, st>>>(h->B, h->s, h->fix_list, h->ctrl, d.H, d.W, d.K, d.S,
                                            exact, h->den, h->C, h->bw_flag);
   // 3. lambda planes

@@ -141,7 +141,7 @@ cudaError_t launch_bruteforce(const hdf_desc& d, const float* f, const void* p, 
   BruteArgs a{f, p, g, d.H, d.W, d.n, d.rho, d.S,
               (p == (const void*)f && d.rho == d.n && d.guide_dtype == HDF_GUIDE_F32) ? 1 : 0,
               (float)(1.0 / (2.0 * d.sigma_r * d.sigma_r))};
-  const Taps taps = make_taps(d.sigma_s, d.S);
+  const Taps taps = make_taps(d.sigma_s, d.S, d.spatial);
   if (d.guide_dtype == HDF_GUIDE_BF16) return launch_brute_c<__nv_bfloat16>(a, taps, st);
   return launch_brute_c<float>(a, taps, st);
 }

@@ -101,13 +101,14 @@ cudaError_t launch_filter(hdf_handle* h, const float* f, float* g, cudaStream_t 
   if (SB < 0) return cudaErrorInvalidValue;
   const int P = (d.n == 1 || SB > 16) ? 2 : 4;
   // Taps centred in the bucket: w[SB + j] = omega_1(j) for |j| <= S, 0 beyond.
-  Taps exact = make_taps(d.sigma_s, d.S);
+  Taps exact = make_taps(d.sigma_s, d.S, d.spatial);
   Taps taps;
   for (int t = 0; t < 2 * HDF_MAX_S + 1; ++t) taps.w[t] = 0.0f;
   for (int j = -d.S; j <= d.S; ++j) taps.w[SB + j] = exact.w[d.S + j];
   cudaError_t e = cudaMemsetAsync(h->ctrl + CTRL_FALLBACK, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  FilterArgs a{f, h->B, h->C, g, h->den, h->rmax, h->ctrl, d.H, d.W, d.n};
+  FilterArgs a{f, h->B, h->C, g, h->den, h->rmax, h->ctrl, d.H, d.W, d.n,
+               d.spatial == HDF_SPATIAL_BOX ? 1 : 0, d.S};
   e = launch_filter_sb(SB, P, a, taps, st);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;

@@ -50,6 +50,10 @@ def test_argument_errors_without_device_work(L):
     bad = L.hdf_desc.from_buffer_copy(d)
     bad.S = L.HDF_MAX_S + 1
     assert lib.hdf_create(C.byref(h), C.byref(bad)) == L.HDF_EUNSUPPORTED
+    bad = L.hdf_desc.from_buffer_copy(d)
+    bad.spatial = 7
+    assert lib.hdf_create(C.byref(h), C.byref(bad)) == L.HDF_EINVAL
+    assert lib.hdf_bruteforce(C.byref(bad), None, None, None, None) == L.HDF_EINVAL
     assert lib.hdf_bruteforce(C.byref(d), None, None, None, None) == L.HDF_EINVAL
     assert lib.hdf_apply(None, None, None, None, None) == L.HDF_EINVAL
     assert lib.hdf_status_string(L.HDF_ETIMEOUT).startswith(b"HDF_ETIMEOUT")

@@ -70,6 +70,22 @@ def config(extra=None):
     return c
 
 
+def slowest_rank_ms(ms: float, dist, device) -> float:
+    """The job's time: the maximum over ranks of a rank's timed region (ms)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mps(units_per_rank: int, world: int, steps: int, ms: float) -> float:
+    """Whole-job megapixels per second: every rank filters its own replica
+    (weak scaling), so the job's pixels are world * steps * units_per_rank."""
+    return world * steps * units_per_rank / (ms * 1e-3) / 1e6
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -228,12 +244,8 @@ def run_gpu(args) -> None:
     step_ms = [a.elapsed_time(b) for a, b in ev]
     cluster_ms = [a.elapsed_time(m) for (a, _), m in zip(ev, mid)]
     apply_ms = [m.elapsed_time(b) for (_, b), m in zip(ev, mid)]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * args.steps * H * W / (total_ms * 1e-3) / 1e6
+    total_ms = slowest_rank_ms(sum(step_ms), dist, dev)
+    value = job_mps(H * W, ws, args.steps, total_ms)
 
     # ---- filter-kernel timing (CUDA events around apply only, same stream)
     ta = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -262,12 +274,8 @@ def run_gpu(args) -> None:
         g_pin.copy_(g, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = ws * args.steps * H * W / (e2e_ms * 1e-3) / 1e6
+    e2e_ms = slowest_rank_ms(e0.elapsed_time(e1), dist, dev)
+    e2e_value = job_mps(H * W, ws, args.steps, e2e_ms)
     nbytes = f_host.nbytes
 
     # ---- brute force on the same GPU (Eq. (1)-(2)) and the accuracy of the fast filter
@@ -284,6 +292,29 @@ def run_gpu(args) -> None:
     mse = float(torch.mean((g.double() - gb.double()) ** 2).item())
     psnr = float("inf") if mse == 0 else -10.0 * np.log10(mse)
     st = flt.stats()
+
+    # ---- the box spatial kernel (omega = 1 on W, Sec. III's NLM kernel) on the
+    # same image and centres: apply-only time and PSNR against its brute force
+    fb = api.HDFilter(H, W, 31, 31, K, WORKLOAD["sigma_s"], WORKLOAD["sigma_r"], S=15, spatial="box")
+    fb.set_centers(flt.get_centers())
+    gbx = torch.empty_like(f)
+    fb.apply(f, f, gbx)
+    tb = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        tb[i][0].record(stream)
+        fb.apply(f, f, gbx)
+        tb[i][1].record(stream)
+    torch.cuda.synchronize()
+    box_ms = statistics.median(a.elapsed_time(b) for a, b in tb)
+    gbb = api.bruteforce(f, None, WORKLOAD["sigma_s"], WORKLOAD["sigma_r"], S=15, spatial="box")
+    torch.cuda.synchronize()
+    bmse = float(torch.mean((gbx.double() - gbb.double()) ** 2).item())
+    box = {"spatial": "box, S=15 (31x31 window), same centres", "apply_ms": box_ms,
+           "apply_mps": H * W / (box_ms * 1e-3) / 1e6,
+           "psnr_vs_box_bruteforce_db": float("inf") if bmse == 0 else -10.0 * np.log10(bmse)}
+    fb.close()
 
     if rank != 0:
         if dist:
@@ -343,6 +374,7 @@ def run_gpu(args) -> None:
             "bruteforce_gpu": {"value": npx / (brute_ms * 1e-3) / 1e6, "unit": UNIT,
                                "ms": brute_ms},
             "psnr_vs_bruteforce_db": psnr,
+            "box_kernel": box,
             "stats": st}
     print(json.dumps(line), flush=True)
     if dist:

@@ -314,7 +314,9 @@ def fast_filter(f: np.ndarray, p: np.ndarray, mu: np.ndarray, sigma_s: float,
       A (Eq. (12)) and its pseudo-inverse;
       for every pixel: b_k(i) = phi(mu_k - p(i)), u_k(i) = b_k(i) f(i);
       c(i) = A^+ b(i)                         (Eq. (11), ``variant='opt'``)
-        or c(i) = e_s, s the nearest centre  (Eq. (17), ``variant='indicator'``);
+        or c(i) = e_s, s the nearest centre  (Eq. (17), ``variant='indicator'``)
+        or the per-pixel least-squares fit   (Eq. (LS), ``variant='ls'``, see
+           ``ls_coefficients``; small images only);
       v = sum_k c_k (omega * u_k), r = sum_k c_k (omega * b_k);
       g_hat = v / r                          (Eq. (15)-(16)).
 
@@ -339,6 +341,8 @@ def fast_filter(f: np.ndarray, p: np.ndarray, mu: np.ndarray, sigma_s: float,
         C = np.einsum("kl,lhw->khw", A_pinv, B)
     elif variant == "indicator":
         C = (np.arange(K)[:, None, None] == s[None]).astype(np.float64)
+    elif variant == "ls":
+        C = ls_coefficients(p, mu, sigma_r, S)
     else:
         raise ValueError(variant)
     v = np.zeros((n, H, W))
@@ -364,6 +368,34 @@ def fast_filter(f: np.ndarray, p: np.ndarray, mu: np.ndarray, sigma_s: float,
     if return_stats:
         return g, dict(fallback=int(fallback.sum()), A=A, A_pinv=A_pinv)
     return g
+
+
+def ls_coefficients(p: np.ndarray, mu: np.ndarray, sigma_r: float, S: int) -> np.ndarray:
+    """The coefficients of the per-pixel least-squares problem (LS) of Sec. II:
+    c(i) minimises sum_{x in Theta_i} (phi(x - p(i)) - sum_k c_k phi(x - mu_k))^2
+    over Theta_i = {p(i - j) : j in W}, the guide values of i's window.
+
+    Readings: Theta_i is taken with multiplicity (one term per window
+    position, positions outside the image left out, as in the sums of
+    Eq. (1)-(2)); where the problem has several minimisers the minimum-norm
+    one is taken (numpy's SVD least squares).  One solve per pixel: the paper
+    calls this impractically slow and keeps it only to compare with Eq. (11)
+    (its Fig. 6); it is here for that comparison on small images.
+    Returns C (K, H, W)."""
+    p = np.asarray(p, dtype=np.float64)
+    mu = np.asarray(mu, dtype=np.float64)
+    rho, H, W = p.shape
+    K = mu.shape[0]
+    C = np.empty((K, H, W))
+    for y in range(H):
+        for x in range(W):
+            ya, yb = max(0, y - S), min(H, y + S + 1)
+            xa, xb = max(0, x - S), min(W, x + S + 1)
+            theta = p[:, ya:yb, xa:xb].reshape(rho, -1).T                  # (|Theta_i|, rho)
+            M = range_kernel(((theta[:, None, :] - mu[None]) ** 2).sum(axis=2), sigma_r)
+            t = range_kernel(((theta - p[:, y, x][None]) ** 2).sum(axis=1), sigma_r)
+            C[:, y, x] = np.linalg.lstsq(M, t, rcond=None)[0]
+    return C
 
 
 def fast_filter_at(f: np.ndarray, p: np.ndarray, mu: np.ndarray, sigma_s: float,

@@ -277,11 +277,57 @@ def conv_cols(x: np.ndarray, w1: np.ndarray) -> np.ndarray:
     return np.swapaxes(conv_rows(np.swapaxes(x, -1, -2), w1), -1, -2)
 
 
+def young_coefficients(sigma_s: float):
+    """Coefficients of Young and van Vliet's third-order recursive Gaussian
+    (Signal Processing 44, 1995), the O(1) convolution the paper uses for its
+    Gaussian spatial kernel (Sec. II-C): q from sigma (their Eq. (11b)),
+    b0..b3 (Eq. (8c)) and the gain B = 1 - (b1 + b2 + b3) / b0.  Returns
+    (B, a1, a2, a3) with a_i = b_i / b0, so that the causal pass is
+    w[t] = B x[t] + a1 w[t-1] + a2 w[t-2] + a3 w[t-3].  Defined for
+    sigma >= 0.5."""
+    s = float(sigma_s)
+    if s >= 2.5:
+        q = 0.98711 * s - 0.96330
+    elif s >= 0.5:
+        q = 3.97156 - 4.14554 * math.sqrt(1.0 - 0.26891 * s)
+    else:
+        raise ValueError("Young's recursive Gaussian needs sigma >= 0.5")
+    b0 = 1.57825 + 2.44413 * q + 1.4281 * q * q + 0.422205 * q ** 3
+    b1 = 2.44413 * q + 2.85619 * q * q + 1.26661 * q ** 3
+    b2 = -(1.4281 * q * q + 1.26661 * q ** 3)
+    b3 = 0.422205 * q ** 3
+    return 1.0 - (b1 + b2 + b3) / b0, b1 / b0, b2 / b0, b3 / b0
+
+
+def young_1d(x: np.ndarray, sigma_s: float, axis: int = -1) -> np.ndarray:
+    """The recursive Gaussian along one axis: the causal pass from the first
+    sample (zero state before it), then the anticausal pass over its output
+    from the last sample (zero state after it):
+      w[t] = B x[t] + a1 w[t-1] + a2 w[t-2] + a3 w[t-3],
+      y[t] = B w[t] + a1 y[t+1] + a2 y[t+2] + a3 y[t+3].
+    Reading: the paper is silent on the boundary; zero states match the zero
+    extension used everywhere else.  scipy's lfilter runs each pass (a
+    library primitive; the tests pin it against a literal loop)."""
+    from scipy.signal import lfilter
+    B, a1, a2, a3 = young_coefficients(sigma_s)
+    num, den = [B], [1.0, -a1, -a2, -a3]
+    x = np.asarray(x, dtype=np.float64)
+    w = lfilter(num, den, x, axis=axis)
+    y = lfilter(num, den, np.flip(w, axis=axis), axis=axis)
+    return np.flip(y, axis=axis)
+
+
 def spatial_conv(x: np.ndarray, sigma_s: float, S: int, spatial: str = "gauss") -> np.ndarray:
     """(omega * x)(i) = sum_{j in W} omega(j) x(i - j) over the window
     W = [-S, S]^2, zero extension outside the image.  omega factorises, so
     the 2-D sum is done as a row pass followed by a column pass; the tests
-    pin this against the direct 2-D sum."""
+    pin this against the direct 2-D sum.  ``spatial='young'``: the Gaussian
+    convolution by Young's recursion instead (rows, then columns; S unused),
+    the paper's O(1) method -- an approximation of a normalised Gaussian of
+    standard deviation sigma_s over the whole image."""
+    if spatial == "young":
+        return young_1d(young_1d(np.asarray(x, dtype=np.float64), sigma_s, axis=-1),
+                        sigma_s, axis=-2)
     w1 = spatial_weights_1d(sigma_s, S, spatial)
     return conv_cols(conv_rows(np.asarray(x, dtype=np.float64), w1), w1)
 
@@ -325,8 +371,9 @@ def fast_filter(f: np.ndarray, p: np.ndarray, mu: np.ndarray, sigma_s: float,
     the pixel falls back to the indicator value v_s(i)/r_s(i) (Eq. (18)) with s
     the nearest centre, and to f(i) if r_s(i) is 0 as well.
 
-    ``spatial``: 'gauss' (Sec. III's Gaussian omega) or 'box' (omega = 1 on
-    W, Sec. III's kernel for nonlocal means).
+    ``spatial``: 'gauss' (Sec. III's Gaussian omega), 'box' (omega = 1 on
+    W, Sec. III's kernel for nonlocal means) or 'young' (the Gaussian by
+    Young's recursion, Sec. II-C's O(1) convolution; S unused).
     Returns g_hat (n, H, W) [, dict(fallback=count)]."""
     f = np.asarray(f, dtype=np.float64)
     p = np.asarray(p, dtype=np.float64)

@@ -59,8 +59,16 @@ enum { HDF_GUIDE_F32 = 0, HDF_GUIDE_BF16 = 1 };
 enum { HDF_COEF_OPT = 0,        /* c(i) = A^+ b(i), Eq. (11) */
        HDF_COEF_INDICATOR = 1   /* c(i) = e_s, s the nearest centre, Eq. (17) */ };
 enum { HDF_SPATIAL_GAUSS = 0,   /* omega(j) = exp(-|j|^2 / 2 sigma_s^2) on W (Sec. III) */
-       HDF_SPATIAL_BOX = 1      /* omega(j) = 1 on W, the kernel Sec. III uses for nonlocal
-                                   means; sigma_s only sets S when S = 0 */ };
+       HDF_SPATIAL_BOX = 1,     /* omega(j) = 1 on W, the kernel Sec. III uses for nonlocal
+                                   means; sigma_s only sets S when S = 0 */
+       HDF_SPATIAL_YOUNG = 2    /* the Gaussian by Young and van Vliet's recursive filter,
+                                   the O(1) convolution Sec. II-C names: causal then
+                                   anticausal third-order recursions along rows, then
+                                   columns, zero states at the borders; sigma_s >= 0.5, S
+                                   unused by the convolutions.  hdf_apply only: the batch,
+                                   hdf_apply_static and hdf_backward return
+                                   HDF_EUNSUPPORTED; hdf_bruteforce computes the exact
+                                   Gaussian it approximates */ };
 
 /* Limits of this build. */
 #define HDF_MAX_K 64           /* clusters */

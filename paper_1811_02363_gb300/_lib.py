@@ -12,7 +12,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libhdfilter.so")
 HDF_OK, HDF_EINVAL, HDF_ENOMEM, HDF_ECUDA, HDF_ETIMEOUT, HDF_EDOMAIN, HDF_EUNSUPPORTED = range(7)
 HDF_GUIDE_F32, HDF_GUIDE_BF16 = 0, 1
 HDF_COEF_OPT, HDF_COEF_INDICATOR = 0, 1
-HDF_SPATIAL_GAUSS, HDF_SPATIAL_BOX = 0, 1
+HDF_SPATIAL_GAUSS, HDF_SPATIAL_BOX, HDF_SPATIAL_YOUNG = 0, 1, 2
 HDF_MAX_K, HDF_MAX_RHO, HDF_MAX_S, HDF_MAX_N = 64, 64, 32, 256
 
 

@@ -48,7 +48,8 @@ def make_desc(H, W, n, rho, K, sigma_s, sigma_r, S=0, guide_dtype="f32", coef="o
     d.sigma_s, d.sigma_r = float(sigma_s), float(sigma_r)
     d.guide_dtype = {"f32": L.HDF_GUIDE_F32, "bf16": L.HDF_GUIDE_BF16}[guide_dtype]
     d.coef = {"opt": L.HDF_COEF_OPT, "indicator": L.HDF_COEF_INDICATOR}[coef]
-    d.spatial = {"gauss": L.HDF_SPATIAL_GAUSS, "box": L.HDF_SPATIAL_BOX}[spatial]
+    d.spatial = {"gauss": L.HDF_SPATIAL_GAUSS, "box": L.HDF_SPATIAL_BOX,
+                 "young": L.HDF_SPATIAL_YOUNG}[spatial]
     return d
 
 

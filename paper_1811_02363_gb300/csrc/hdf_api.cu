@@ -30,7 +30,10 @@ hdf_status check_desc(hdf_desc* d) {
   if (d->S == 0) d->S = (int)ceil(3.0 * d->sigma_s);
   if (d->guide_dtype != HDF_GUIDE_F32 && d->guide_dtype != HDF_GUIDE_BF16) return HDF_EINVAL;
   if (d->coef != HDF_COEF_OPT && d->coef != HDF_COEF_INDICATOR) return HDF_EINVAL;
-  if (d->spatial != HDF_SPATIAL_GAUSS && d->spatial != HDF_SPATIAL_BOX) return HDF_EINVAL;
+  if (d->spatial != HDF_SPATIAL_GAUSS && d->spatial != HDF_SPATIAL_BOX &&
+      d->spatial != HDF_SPATIAL_YOUNG)
+    return HDF_EINVAL;
+  if (d->spatial == HDF_SPATIAL_YOUNG && !(d->sigma_s >= 0.5)) return HDF_EINVAL;
   if (d->K > HDF_MAX_K || d->rho > HDF_MAX_RHO || d->S > HDF_MAX_S || d->n > HDF_MAX_N)
     return HDF_EUNSUPPORTED;
   if ((long long)d->H * d->W >= (1LL << 31)) return HDF_EUNSUPPORTED;
@@ -114,6 +117,9 @@ hdf_status hdf_create(hdf_handle** out, const hdf_desc* desc) {
   ok &= dalloc(&h->bw_gam, K * N) == cudaSuccess;
   ok &= dalloc(&h->bw_bet, K * N) == cudaSuccess;
   ok &= dalloc(&h->bw_flag, N) == cudaSuccess;
+  h->young_T = nullptr;
+  if (d.spatial == HDF_SPATIAL_YOUNG)
+    ok &= dalloc(&h->young_T, K * (size_t)(d.n + 1) * N) == cudaSuccess;
   {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -160,6 +166,7 @@ void hdf_destroy(hdf_handle* h) {
   cudaFree(h->bw_gam);
   cudaFree(h->bw_bet);
   cudaFree(h->bw_flag);
+  cudaFree(h->young_T);
   cudaFree(h->cl_ws);
   cudaFree(h->nlm_ws);
   delete h;

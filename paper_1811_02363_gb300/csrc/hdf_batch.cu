@@ -430,6 +430,7 @@ hdf_status hdf_batch_create(hdf_batch** out, int count, const hdf_desc* descs) {
     m.d = descs[i];
     hdf_status s = hdf::check_desc(&m.d);
     if (s != HDF_OK) { delete b; return s; }
+    if (m.d.spatial == HDF_SPATIAL_YOUNG) { delete b; return HDF_EUNSUPPORTED; }   // FIR tiles only
     m.N = m.d.H * m.d.W;
     m.SB = hdf::filter_bucket(m.d.S);
     if (m.SB < 0) { delete b; return HDF_EUNSUPPORTED; }

@@ -76,6 +76,7 @@ struct hdf_handle {
   float* bw_gam;      // K x N gamma_k
   float* bw_bet;      // K x N direct part of dL/db_k
   uint8_t* bw_flag;   // N pixels that took the denominator guard
+  float* young_T;     // K x (n+1) x N row-filtered planes (recursive Gaussian only)
   void* nlm_ws;       // NLM guide workspace
   size_t nlm_ws_bytes;
 };
@@ -98,6 +99,7 @@ cudaError_t launch_fit_batch(const FitJob* jobs, int njobs, int Kmax, cudaStream
 cudaError_t launch_set_int(int* p, int v, cudaStream_t st);
 cudaError_t launch_rangemap(hdf_handle* h, const void* p, cudaStream_t st);
 cudaError_t launch_filter(hdf_handle* h, const float* f, float* g, cudaStream_t st);
+cudaError_t launch_young(hdf_handle* h, const float* f, float* g, cudaStream_t st);
 cudaError_t launch_bruteforce(const hdf_desc& d, const float* f, const void* p, float* g,
                               cudaStream_t st);
 cudaError_t cluster_init(hdf_handle* h);                          // one-entry table, at create

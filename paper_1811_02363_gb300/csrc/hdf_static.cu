@@ -77,6 +77,7 @@ extern "C" hdf_status hdf_apply_static(const hdf_desc* desc, const float* d_mu, 
   hdf_desc d = *desc;
   hdf_status st = validate(&d, K);
   if (st != HDF_OK) return st;
+  if (d.spatial == HDF_SPATIAL_YOUNG) return HDF_EUNSUPPORTED;   // needs per-plane scratch
   d.K = K;
   const size_t N = (size_t)d.H * d.W;
 

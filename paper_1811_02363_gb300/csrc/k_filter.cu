@@ -97,6 +97,7 @@ int filter_bucket(int S) {
 
 cudaError_t launch_filter(hdf_handle* h, const float* f, float* g, cudaStream_t st) {
   const hdf_desc& d = h->d;
+  if (d.spatial == HDF_SPATIAL_YOUNG) return launch_young(h, f, g, st);
   const int SB = filter_bucket(d.S);
   if (SB < 0) return cudaErrorInvalidValue;
   const int P = (d.n == 1 || SB > 16) ? 2 : 4;

@@ -102,7 +102,8 @@ typedef struct {
 
 /* Validate `desc`, fill in S if 0, and allocate the device workspace of one
  * filter instance (centres, A^+, per-pixel range maps and coefficients,
- * clustering scratch).  Synchronous; the only call that allocates.
+ * clustering scratch; with HDF_SPATIAL_YOUNG also K (n+1) H W floats of
+ * staged planes).  Synchronous; the only call that allocates.
  * Sec. II (Algorithm 1 needs mu, A^+ and the b_k, c_k maps).
  * Errors: HDF_EINVAL (bad desc), HDF_EUNSUPPORTED (beyond HDF_MAX_*),
  * HDF_ENOMEM. */

@@ -13,25 +13,65 @@ namespace hdf {
 
 constexpr float kGuardRel = 1e-6f;   // guard: sum_k c_k r_k <= 1e-6 max_k r_k
 
+// Shared-memory tables of the range-map kernels: the centres transposed,
+// smu[d][k], and A^+ by rows, spi[k][l], both with rows of KP = K rounded up
+// to 4 floats (zero padding), so that a 16-byte load brings 4 centres.
+__host__ __device__ constexpr int rm_pitch(int K) { return (K + 3) & ~3; }
+__host__ __device__ constexpr int rm_smem_floats(int K, int rho) { return rm_pitch(K) * (rho + K); }
+
+__device__ __forceinline__ void rangemap_stage(const float* __restrict__ mu,
+                                               const float* __restrict__ pinv, int K, int rho,
+                                               float* sm) {
+  const int KP = rm_pitch(K);
+  float* smu = sm;
+  float* spi = sm + rho * KP;
+  for (int i = threadIdx.x; i < rho * KP; i += blockDim.x) {
+    const int d = i / KP, k = i - d * KP;
+    smu[i] = k < K ? mu[k * rho + d] : 0.0f;
+  }
+  for (int i = threadIdx.x; i < K * KP; i += blockDim.x) {
+    const int k = i / KP, l = i - k * KP;
+    spi[i] = l < K ? pinv[k * K + l] : 0.0f;
+  }
+}
+
 // b_k(i) = phi(mu_k - p(i)) (Eq. (12)) from direct differences in FP32;
 // c(i) = A^+ b(i) (Eq. (11)) or e_s (Eq. (17)); s(i) = nearest centre (ties
-// -> lowest k).  smu (K x rho) and spi (K x K) are in shared memory.
+// -> lowest k).  sm holds the tables of rangemap_stage.  The guide values
+// are loaded RB at a time (independent loads in flight); every sum runs in
+// ascending d or l.
 template <int KMAX, typename GT>
 __device__ __forceinline__ void rangemap_pixel(const GT* __restrict__ p, size_t N, size_t pix,
-                                               int rho, int K, const float* smu,
-                                               const float* spi, float inv2sr2, int coef,
-                                               float* __restrict__ B, float* __restrict__ C,
+                                               int rho, int K, const float* sm, float inv2sr2,
+                                               int coef, float* __restrict__ B,
+                                               float* __restrict__ C,
                                                uint8_t* __restrict__ s_out) {
+  constexpr int RB = 8;
+  constexpr int K4 = KMAX / 4;
+  const int KP = rm_pitch(K);
+  const float* smu = sm;
+  const float* spi = sm + rho * KP;
   float d2[KMAX];
 #pragma unroll
   for (int k = 0; k < KMAX; ++k) d2[k] = 0.0f;
-  for (int d = 0; d < rho; ++d) {
-    const float x = guide_load(p, (size_t)d * N + pix);
+  for (int d0 = 0; d0 < rho; d0 += RB) {
+    float x[RB];
 #pragma unroll
-    for (int k = 0; k < KMAX; ++k) {
-      if (k < K) {
-        const float t = x - smu[k * rho + d];
-        d2[k] = fmaf(t, t, d2[k]);
+    for (int u = 0; u < RB; ++u) x[u] = (d0 + u < rho) ? guide_load(p, (size_t)(d0 + u) * N + pix) : 0.0f;
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      if (d0 + u >= rho) break;
+      const float4* m4 = reinterpret_cast<const float4*>(smu + (d0 + u) * KP);
+#pragma unroll
+      for (int q = 0; q < K4; ++q) {
+        if (4 * q < K) {
+          const float4 m = m4[q];
+          const float t0 = x[u] - m.x, t1 = x[u] - m.y, t2 = x[u] - m.z, t3 = x[u] - m.w;
+          d2[4 * q] = fmaf(t0, t0, d2[4 * q]);
+          d2[4 * q + 1] = fmaf(t1, t1, d2[4 * q + 1]);
+          d2[4 * q + 2] = fmaf(t2, t2, d2[4 * q + 2]);
+          d2[4 * q + 3] = fmaf(t3, t3, d2[4 * q + 3]);
+        }
       }
     }
   }
@@ -52,9 +92,17 @@ __device__ __forceinline__ void rangemap_pixel(const GT* __restrict__ p, size_t 
       float c;
       if (coef == HDF_COEF_OPT) {
         c = 0.0f;
+        const float4* r4 = reinterpret_cast<const float4*>(spi + k * KP);
 #pragma unroll
-        for (int l = 0; l < KMAX; ++l)
-          if (l < K) c = fmaf(spi[k * K + l], b[l], c);
+        for (int q = 0; q < K4; ++q) {
+          if (4 * q < K) {   // padded entries are 0 and b beyond K is 0
+            const float4 a = r4[q];
+            c = fmaf(a.x, b[4 * q], c);
+            c = fmaf(a.y, b[4 * q + 1], c);
+            c = fmaf(a.z, b[4 * q + 2], c);
+            c = fmaf(a.w, b[4 * q + 3], c);
+          }
+        }
       } else {
         c = (k == s) ? 1.0f : 0.0f;
       }
@@ -77,7 +125,16 @@ __device__ __forceinline__ void divide_pixel(float* __restrict__ g, const float*
     return;
   }
   const float inv = 1.0f / D;
-  for (int c = 0; c < n; ++c) g[(size_t)c * N + pix] *= inv;
+  constexpr int CB = 8;   // channels whose loads are issued together
+  for (int c0 = 0; c0 < n; c0 += CB) {
+    float v[CB];
+#pragma unroll
+    for (int u = 0; u < CB; ++u)
+      if (c0 + u < n) v[u] = g[(size_t)(c0 + u) * N + pix];
+#pragma unroll
+    for (int u = 0; u < CB; ++u)
+      if (c0 + u < n) g[(size_t)(c0 + u) * N + pix] = v[u] * inv;
+  }
 }
 
 // Indicator value v_s(i) / r_s(i) of Eq. (18) for channel ch of a guarded

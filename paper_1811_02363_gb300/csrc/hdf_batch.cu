@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "batch.cuh"
+#include "combine.cuh"
 
 namespace hdf {
 namespace {
@@ -397,7 +398,7 @@ cudaError_t enqueue(hdf_batch* b, int flags, cudaStream_t st, cudaEvent_t* ev) {
   mark(4);
   if (e == cudaSuccess)
     e = launch_batch_rangemap(b->d_rm, b->d_rm_block0, b->count, b->rm_blocks, b->Kmax,
-                              b->Kmax * b->rho_max + b->Kmax * b->Kmax, st);
+                              rm_smem_floats(b->Kmax, b->rho_max), st);
   mark(5);
   if (e == cudaSuccess) e = tile_launch(b, b->nitems, b->smem_tile, st);
   mark(6);

@@ -52,25 +52,22 @@ __global__ void batch_to_bf16_kernel(const GuideJob* __restrict__ jobs, const in
 template <int KMAX>
 __global__ void __launch_bounds__(BK_THREADS)
 batch_rangemap_kernel(const RmJob* __restrict__ jobs, const int* __restrict__ block0, int njobs) {
-  extern __shared__ float sm[];
+  extern __shared__ __align__(16) float sm[];
   __shared__ int s_j;
   if (threadIdx.x == 0) s_j = job_of_block(block0, njobs, blockIdx.x);
   __syncthreads();
   const RmJob& jb = jobs[s_j];
   const int K = jb.ctrl[CTRL_K_EFF];
   const int rho = jb.rho;
-  float* smu = sm;
-  float* spi = sm + K * rho;
-  for (int i = threadIdx.x; i < K * rho; i += BK_THREADS) smu[i] = jb.mu[i];
-  for (int i = threadIdx.x; i < K * K; i += BK_THREADS) spi[i] = jb.pinv[i];
+  rangemap_stage(jb.mu, jb.pinv, K, rho, sm);
   __syncthreads();
   const int pix = (blockIdx.x - block0[s_j]) * BK_THREADS + threadIdx.x;
   if (pix >= jb.N) return;
   if (jb.p_bf16)
-    rangemap_pixel<KMAX>((const __nv_bfloat16*)jb.p, (size_t)jb.N, (size_t)pix, rho, K, smu, spi,
+    rangemap_pixel<KMAX>((const __nv_bfloat16*)jb.p, (size_t)jb.N, (size_t)pix, rho, K, sm,
                          jb.inv2sr2, jb.coef, jb.B, jb.C, jb.s);
   else
-    rangemap_pixel<KMAX>((const float*)jb.p, (size_t)jb.N, (size_t)pix, rho, K, smu, spi,
+    rangemap_pixel<KMAX>((const float*)jb.p, (size_t)jb.N, (size_t)pix, rho, K, sm,
                          jb.inv2sr2, jb.coef, jb.B, jb.C, jb.s);
 }
 

@@ -19,22 +19,19 @@ rangemap_kernel(const GT* __restrict__ p, int N, int rho, const float* __restric
                 const float* __restrict__ pinv, const int* __restrict__ ctrl, float inv2sr2,
                 int coef, float* __restrict__ B, float* __restrict__ C,
                 uint8_t* __restrict__ s_out) {
-  extern __shared__ float sm[];
+  extern __shared__ __align__(16) float sm[];
   const int K = ctrl[CTRL_K_EFF];
-  float* smu = sm;                 // K x rho
-  float* spi = sm + K * rho;       // K x K
-  for (int i = threadIdx.x; i < K * rho; i += blockDim.x) smu[i] = mu[i];
-  for (int i = threadIdx.x; i < K * K; i += blockDim.x) spi[i] = pinv[i];
+  rangemap_stage(mu, pinv, K, rho, sm);
   __syncthreads();
   const int pix = blockIdx.x * blockDim.x + threadIdx.x;
   if (pix >= N) return;
-  rangemap_pixel<KMAX>(p, (size_t)N, (size_t)pix, rho, K, smu, spi, inv2sr2, coef, B, C, s_out);
+  rangemap_pixel<KMAX>(p, (size_t)N, (size_t)pix, rho, K, sm, inv2sr2, coef, B, C, s_out);
 }
 
 template <int KMAX>
 cudaError_t launch_rm(hdf_handle* h, const void* p, cudaStream_t st) {
   const hdf_desc& d = h->d;
-  const size_t smem = sizeof(float) * ((size_t)d.K * d.rho + (size_t)d.K * d.K);
+  const size_t smem = sizeof(float) * (size_t)rm_smem_floats(d.K, d.rho);   // K_eff <= K
   const float inv2sr2 = (float)(1.0 / (2.0 * d.sigma_r * d.sigma_r));
   const int grid = (h->N + RM_THREADS - 1) / RM_THREADS;
   if (d.guide_dtype == HDF_GUIDE_BF16)

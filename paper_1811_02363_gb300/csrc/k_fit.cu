@@ -4,11 +4,13 @@
 // between clustering and filtering.
 //
 // Two routes, same result up to rounding:
-//  * Cholesky A = L L^T and A^{-1} = L^{-T} L^{-1}, taken when the Frobenius
-//    bound ||A||_F ||A^{-1}||_F K 2^-52 < 1/2 certifies that every eigenvalue
-//    of A exceeds MATLAB's default tolerance K eps(||A||_2) -- then pinv(A)
-//    is the inverse.  This is the common case (distinct centres make the
-//    Gaussian Gram matrix positive definite) and costs O(K^3/3) FP64 FMAs.
+//  * A = L D L^T (unit lower L, square-root free Cholesky) and
+//    A^{-1} = L^{-T} D^{-1} L^{-1}, taken when every pivot is positive and
+//    the Frobenius bound ||A||_F ||A^{-1}||_F K 2^-52 < 1/2 certifies that
+//    every eigenvalue of A exceeds MATLAB's default tolerance K eps(||A||_2)
+//    -- then pinv(A) is the inverse.  This is the common case (distinct
+//    centres make the Gaussian Gram matrix positive definite) and costs
+//    O(K^3/2) FP64 FMAs.
 //  * otherwise cyclic Jacobi A = Q diag(lam) Q^T (Golub & Van Loan, symmetric
 //    Schur rotations) and A^+ = sum over |lam| > K eps(max|lam|) of
 //    q q^T / lam, the MATLAB rule.
@@ -29,70 +31,123 @@ __device__ double matlab_tol(double norm2, int K) {
   return (double)K * ldexp(1.0, e - 53);
 }
 
+// Pair p (0 <= p < K (K - 1) / 2) of the strict upper triangle in row-major
+// order -> (k, l), k < l.  Row r starts at r (2K - r - 1) / 2.
+__device__ __forceinline__ void pair_of(int p, int K, int& k, int& l) {
+  const float b = 2.0f * K - 1.0f;
+  int r = (int)floorf((b - sqrtf(b * b - 8.0f * (float)p)) * 0.5f);
+  r = max(0, min(r, K - 2));
+  while (r + 1 <= K - 2 && (r + 1) * (2 * K - r - 2) / 2 <= p) ++r;
+  while (r > 0 && r * (2 * K - r - 1) / 2 > p) --r;
+  k = r;
+  l = p - r * (2 * K - r - 1) / 2 + r + 1;
+}
+
+// Entry t of a lower triangle (b <= a) in row-major order -> (a, b).
+__device__ __forceinline__ void tri_of(int t, int& a, int& b) {
+  int r = (int)floorf((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  r = max(r, 0);
+  while ((r + 1) * (r + 2) / 2 <= t) ++r;
+  while (r * (r + 1) / 2 > t) --r;
+  a = r;
+  b = t - r * (r + 1) / 2;
+}
+
+// FP64 on this part issues at a small fraction of the FP32 rate, so the
+// routes below keep the dependent FP64 steps few: every elimination step is
+// one block-wide phase (one barrier), and the one reciprocal a step needs is
+// taken by the thread that produced the next pivot in the previous phase.
 __device__ void fit_run(const float* __restrict__ mu, int rho, int* ctrl, double inv2sr2,
                         double* __restrict__ pinv64, float* __restrict__ pinv32, double* sm) {
   const int K = ctrl[CTRL_K_EFF];
   const int tid = threadIdx.x, nt = blockDim.x;
-  double* A = sm;              // K x K
-  double* L = A + K * K;       // K x K (Cholesky factor, then Jacobi eigenvectors)
-  double* X = L + K * K;       // K x K (inverse / working matrix)
+  double* A = sm;              // K x K (kept for the eigen route)
+  double* L = A + K * K;       // K x K: L D L^T in place, then Jacobi eigenvectors
+  double* X = L + K * K;       // K x K: L^{-1}, then the working matrix of Jacobi
   __shared__ int s_flag;
   __shared__ double s_red[FIT_THREADS];
   __shared__ double s_cs[2];
+  __shared__ double s_rd[HDF_MAX_K];   // 1 / d_j
 
-  for (int idx = tid; idx < K * K; idx += nt) {
-    const int k = idx / K, l = idx % K;
+  // A_kl = phi(mu_k - mu_l) for k < l (symmetric; phi(0) = 1 on the diagonal)
+  for (int p = tid; p < K * (K - 1) / 2; p += nt) {
+    int k, l;
+    pair_of(p, K, k, l);
     double d2 = 0.0;
     for (int d = 0; d < rho; ++d) {
       const double t = (double)mu[k * rho + d] - (double)mu[l * rho + d];
       d2 += t * t;
     }
-    A[idx] = exp(-d2 * inv2sr2);
-    L[idx] = 0.0;
+    const double v = exp(-d2 * inv2sr2);
+    A[k * K + l] = v;
+    A[l * K + k] = v;
+    L[l * K + k] = v;   // the lower triangle is the factorisation's copy
   }
-  if (tid == 0) s_flag = 1;
+  for (int k = tid; k < K; k += nt) {
+    A[k * K + k] = 1.0;
+    L[k * K + k] = 1.0;
+  }
+  for (int idx = tid; idx < K * K; idx += nt) X[idx] = (idx / K == idx % K) ? 1.0 : 0.0;
+  if (tid == 0) {
+    s_flag = 1;
+    s_rd[0] = 1.0;   // d_0 = A_00 = 1
+  }
   __syncthreads();
 
-  // ---- Cholesky, column by column.
-  for (int j = 0; j < K; ++j) {
-    if (tid == 0) {
-      double s = A[j * K + j];
-      for (int m = 0; m < j; ++m) s -= L[j * K + m] * L[j * K + m];
-      if (!(s > 0.0)) s_flag = 0;
-      L[j * K + j] = s > 0.0 ? sqrt(s) : 1.0;
+  // ---- L D L^T, right-looking: in step j the lower trailing entries
+  // (i >= l > j) take L_il -= L_ij L_lj / d_j with column j still unscaled
+  // (L_ij = A'_ij); the thread of entry (j+1, j+1) then holds d_{j+1} and
+  // takes its reciprocal.  Columns are scaled by 1 / d_j afterwards.
+  for (int j = 0; j + 1 < K; ++j) {
+    const double rdj = s_rd[j];
+    const int m = K - 1 - j;
+    for (int t = tid; t < m * (m + 1) / 2; t += nt) {
+      int ai, bl;
+      tri_of(t, ai, bl);
+      const int i = j + 1 + ai, l = j + 1 + bl;
+      const double v = L[i * K + l] - L[i * K + j] * (L[l * K + j] * rdj);
+      L[i * K + l] = v;
+      if (t == 0) {   // (j+1, j+1): the next pivot
+        if (!(v > 0.0)) s_flag = 0;
+        s_rd[j + 1] = v > 0.0 ? __drcp_rn(v) : 0.0;
+      }
     }
     __syncthreads();
-    if (!s_flag) break;
-    const double djj = L[j * K + j];
-    for (int i = j + 1 + tid; i < K; i += nt) {
-      double s = A[i * K + j];
-      for (int m = 0; m < j; ++m) s -= L[i * K + m] * L[j * K + m];
-      L[i * K + j] = s / djj;
-    }
-    __syncthreads();
+    if (s_rd[j + 1] == 0.0) break;   // written in this step only: a uniform exit
   }
   bool full_rank = false;
   if (tid == 0) ctrl[CTRL_RANKDEF] = 0;
   if (s_flag) {
-    // Column c of L^{-1} by forward substitution (one thread per column),
-    // stored transposed: X[c*K + i] = (L^{-1})_{i c}.
-    for (int c = tid; c < K; c += nt) {
-      for (int i = 0; i < K; ++i) {
-        double s = (i == c) ? 1.0 : 0.0;
-        for (int m = c; m < i; ++m) s -= L[i * K + m] * X[c * K + m];
-        X[c * K + i] = (i < c) ? 0.0 : s / L[i * K + i];
-      }
+    for (int t = tid; t < K * (K - 1) / 2; t += nt) {   // L_ij = A'_ij / d_j, i > j
+      int ai, bj;
+      tri_of(t, ai, bj);
+      L[(ai + 1) * K + bj] *= s_rd[bj];
     }
     __syncthreads();
-    // A^{-1}_{kl} = sum_m (L^{-1})_{m k} (L^{-1})_{m l}; written to pinv64.
+    // X = L^{-1} (unit lower), right-looking: in step m the rows i > m take
+    // X_ic -= L_im X_mc for c <= m (row m is final after step m - 1).
+    for (int m = 0; m + 1 < K; ++m) {
+      const int w = m + 1;
+      for (int t = tid; t < (K - 1 - m) * w; t += nt) {
+        const int i = m + 1 + t / w, c = t % w;
+        X[i * K + c] -= L[i * K + m] * X[m * K + c];
+      }
+      __syncthreads();
+    }
+    // A^{-1}_kl = sum_{m >= max(k, l)} X_mk X_ml / d_m: Y = D^{-1} X into L
+    // (the factor is no longer needed), then one pass per entry k <= l.
+    for (int idx = tid; idx < K * K; idx += nt) L[idx] = X[idx] * s_rd[idx / K];
+    __syncthreads();
     double fx = 0.0, fa = 0.0;
     for (int idx = tid; idx < K * K; idx += nt) {
-      const int k = idx / K, l = idx % K;
-      double s = 0.0;
-      for (int m = (k > l ? k : l); m < K; ++m) s += X[k * K + m] * X[l * K + m];
-      pinv64[idx] = s;
-      fx += s * s;
+      const int k = idx % K, l = idx / K;   // a warp shares l: equal trip counts
       fa += A[idx] * A[idx];
+      if (k > l) continue;
+      double s = 0.0;
+      for (int m = l; m < K; ++m) s = fma(L[m * K + k], X[m * K + l], s);
+      pinv64[k * K + l] = s;
+      pinv64[l * K + k] = s;
+      fx += (k == l ? 1.0 : 2.0) * s * s;
     }
     s_red[tid] = fx;
     __syncthreads();

@@ -34,7 +34,14 @@ struct FilterArgs {
   const int* ctrl;
   int H, W, n;
   int box, S;           // box spatial kernel (omega = 1 on W) of half-width S <= SB
+  int vec;              // W % 4 == 0 and f 16-byte aligned: halo rows staged in 16-byte copies
 };
+
+__device__ __forceinline__ void cp_async16(float* smem, const float* gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int bytes = valid ? 16 : 0;   // 0 bytes read: the 4 words are zero-filled
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(bytes));
+}
 
 __device__ __forceinline__ void cp_async4(float* smem, const float* gmem, bool valid) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -58,11 +65,13 @@ struct TileCfg {
   static constexpr int YV = TX * TY * P / NT;          // column-pass outputs per thread
   static constexpr int XH = 16;                         // row-pass outputs per task
   static constexpr int NSEG = TX / XH;
-  static constexpr int NIN = XH + 2 * SB;               // row-pass inputs per task
+  static constexpr int SA = (SB + 3) & ~3;              // staged half-width (16-byte aligned)
+  static constexpr int OFF = SA - SB;                   // first used column of a staged row
+  static constexpr int NIN = XH + 2 * SB + OFF;         // row-pass inputs per task (from the aligned start)
   static constexpr int NIN4 = (NIN + 3) / 4;            // 128-bit loads per task
   static constexpr int HR = TY + 2 * SB;                // halo rows
-  static constexpr int HC = TX + 2 * SB;                // halo columns
-  static constexpr int LD = round_ld((NSEG - 1) * XH + 4 * NIN4);
+  static constexpr int HC = TX + 2 * SA;                // staged columns x0 - SA .. x0 + TX + SA - 1
+  static constexpr int LD = round_ld((NSEG - 1) * XH + 4 * NIN4 > HC ? (NSEG - 1) * XH + 4 * NIN4 : HC);
   static constexpr int LDH = round_ld(TX);
   static constexpr int SF = P * HR * LD;                // floats
   static constexpr int SBF = HR * LD;
@@ -72,29 +81,43 @@ struct TileCfg {
   static_assert(TY % YV == 0 && YV >= 1, "tile height must be a multiple of the per-thread run");
   static_assert(TX * (TY / YV) * P == NT, "one column run per thread");
   static_assert(LD >= HC, "row stride must hold the halo");
+  static_assert(SMEM <= 232448, "shared memory per block");
 };
 
 // XW outputs of the row FIR omega_1 (*) u on one halo row, u = b (plane 0)
 // or b f (the other planes), from 16-byte-aligned shared rows; results to out.
 // tap(t) is the weight of tap t (0 <= t <= 2 SB).
-template <int SB, int XW, class Wt>
-__device__ __forceinline__ void fir_row(const float* __restrict__ brow, const float* __restrict__ frow,
-                                        bool plane0, const Wt& tap, float* __restrict__ out) {
-  constexpr int NIN4 = (XW + 2 * SB + 3) / 4, NTAP = 2 * SB + 1;
+// The inputs of XW row outputs: XW + 2 SB values starting OFF words after the
+// 16-byte-aligned row pointers (b, or b f off plane 0), loaded as float4.
+template <int SB, int XW, int OFF>
+__device__ __forceinline__ void row_inputs(const float* __restrict__ brow,
+                                           const float* __restrict__ frow, bool plane0,
+                                           float (&in)[XW + 2 * SB]) {
+  constexpr int NIN4 = (XW + 2 * SB + OFF + 3) / 4;
   const float4* pb = reinterpret_cast<const float4*>(brow);
   const float4* pf = reinterpret_cast<const float4*>(frow);
-  float in[4 * NIN4];
+  float raw[4 * NIN4];
 #pragma unroll
   for (int t = 0; t < NIN4; ++t) {
     const float4 b = pb[t];
     if (plane0) {
-      in[4 * t] = b.x; in[4 * t + 1] = b.y; in[4 * t + 2] = b.z; in[4 * t + 3] = b.w;
+      raw[4 * t] = b.x; raw[4 * t + 1] = b.y; raw[4 * t + 2] = b.z; raw[4 * t + 3] = b.w;
     } else {
       const float4 v = pf[t];
-      in[4 * t] = b.x * v.x; in[4 * t + 1] = b.y * v.y;
-      in[4 * t + 2] = b.z * v.z; in[4 * t + 3] = b.w * v.w;
+      raw[4 * t] = b.x * v.x; raw[4 * t + 1] = b.y * v.y;
+      raw[4 * t + 2] = b.z * v.z; raw[4 * t + 3] = b.w * v.w;
     }
   }
+#pragma unroll
+  for (int i = 0; i < XW + 2 * SB; ++i) in[i] = raw[i + OFF];
+}
+
+template <int SB, int XW, class Wt, int OFF = 0>
+__device__ __forceinline__ void fir_row(const float* __restrict__ brow, const float* __restrict__ frow,
+                                        bool plane0, const Wt& tap, float* __restrict__ out) {
+  constexpr int NTAP = 2 * SB + 1;
+  float in[XW + 2 * SB];
+  row_inputs<SB, XW, OFF>(brow, frow, plane0, in);
   float h[XW];
 #pragma unroll
   for (int o = 0; o < XW; ++o) h[o] = 0.0f;
@@ -140,26 +163,13 @@ __device__ __forceinline__ void box_sums(int d, const float (&in)[NI], float (&o
 
 // The box kernel's row pass (omega_1 = 1 on [-S, S]): the inputs are loaded
 // as in fir_row, the XW outputs are running window sums.
-template <int SB, int XW>
+template <int SB, int XW, int OFF>
 __device__ __forceinline__ void box_row(const float* __restrict__ brow, const float* __restrict__ frow,
                                         bool plane0, int S, float* __restrict__ out) {
-  constexpr int NIN4 = (XW + 2 * SB + 3) / 4;
-  const float4* pb = reinterpret_cast<const float4*>(brow);
-  const float4* pf = reinterpret_cast<const float4*>(frow);
-  float in[4 * NIN4];
-#pragma unroll
-  for (int t = 0; t < NIN4; ++t) {
-    const float4 b = pb[t];
-    if (plane0) {
-      in[4 * t] = b.x; in[4 * t + 1] = b.y; in[4 * t + 2] = b.z; in[4 * t + 3] = b.w;
-    } else {
-      const float4 v = pf[t];
-      in[4 * t] = b.x * v.x; in[4 * t + 1] = b.y * v.y;
-      in[4 * t + 2] = b.z * v.z; in[4 * t + 3] = b.w * v.w;
-    }
-  }
+  float in[XW + 2 * SB];
+  row_inputs<SB, XW, OFF>(brow, frow, plane0, in);
   float h[XW];
-  box_sums<SB, XW, 4 * NIN4>(SB - S, in, h);
+  box_sums<SB, XW, XW + 2 * SB>(SB - S, in, h);
   float4* ph = reinterpret_cast<float4*>(out);
 #pragma unroll
   for (int o = 0; o < XW / 4; ++o) ph[o] = make_float4(h[4 * o], h[4 * o + 1], h[4 * o + 2], h[4 * o + 3]);
@@ -192,23 +202,41 @@ filter_tile_kernel(const FilterArgs a, const Taps taps) {
   const int gx = x0 + xv;
   const int qgv = chunk * P + qv;        // global plane of this thread's column run
 
-  // ---- staging (cp.async, zero-filled outside the image): a warp copies
-  // whole halo rows, lanes over the columns, so the per-element index math is
-  // a compare and an add.  The column bounds of a lane do not change.
+  // ---- staging (cp.async, zero-filled outside the image) of the columns
+  // x0 - SA .. x0 + TX + SA - 1 (a 16-byte-aligned start; the row pass reads
+  // from column OFF = SA - SB on).  With W % 4 == 0 and aligned planes a
+  // 16-byte chunk is either inside the image or outside it, and a warp copies
+  // CPR chunks of each of its rows; otherwise single words, a warp per row,
+  // lanes over the columns.
   const int lane = tid & 31, warp = tid >> 5;
   constexpr int NW = NT / 32;
-  constexpr int CPL = (HC + 31) / 32;   // columns per lane
+  constexpr int SA = Cfg::SA, OFF = Cfg::OFF;
+  constexpr int CPR = HC / 4;           // 16-byte chunks per staged row
+  constexpr int RPW = (HR + NW - 1) / NW;   // rows per warp
+  constexpr int CPL = (HC + 31) / 32;   // columns per lane (word path)
   unsigned col_ok = 0;                  // bit j: column lane + 32 j inside the image
 #pragma unroll
   for (int j = 0; j < CPL; ++j) {
-    const int c = lane + 32 * j, xx = x0 - SB + c;
+    const int c = lane + 32 * j, xx = x0 - SA + c;
     if (c < HC && xx >= 0 && xx < W) col_ok |= 1u << j;
   }
+  const bool vec = a.vec != 0;
   auto stage_rows = [&](const float* plane, float* dst, int r0, int nrows) {
+    if (vec) {
+      for (int i = lane; i < RPW * CPR; i += 32) {
+        const int rl = i / CPR, ch = i - rl * CPR;
+        const int r = r0 + rl * NW;
+        if (r >= nrows) continue;
+        const int yy = y0 - SB + r, xx = x0 - SA + 4 * ch;
+        const bool ok = yy >= 0 && yy < H && xx >= 0 && xx + 4 <= W;
+        cp_async16(dst + r * LD + 4 * ch, ok ? plane + (size_t)yy * W + xx : plane, ok);
+      }
+      return;
+    }
     for (int r = r0; r < nrows; r += NW) {
       const int yy = y0 - SB + r;
       const bool rok = yy >= 0 && yy < H;
-      const float* grow = plane + (ptrdiff_t)yy * W + (x0 - SB);
+      const float* grow = plane + (ptrdiff_t)yy * W + (x0 - SA);
       float* srow = dst + r * LD;
 #pragma unroll
       for (int j = 0; j < CPL; ++j) {
@@ -277,11 +305,12 @@ filter_tile_kernel(const FilterArgs a, const Taps taps) {
         const int qg = chunk * P + q;
         if (qg > n) continue;
         if constexpr (BOX)
-          box_row<SB, XH>(sB + r * LD + seg * XH, sF + (q * HR + r) * LD + seg * XH, qg == 0, a.S,
-                          sH + (q * HR + r) * LDH + seg * XH);
+          box_row<SB, XH, OFF>(sB + r * LD + seg * XH, sF + (q * HR + r) * LD + seg * XH, qg == 0,
+                               a.S, sH + (q * HR + r) * LDH + seg * XH);
         else
-          fir_row<SB, XH>(sB + r * LD + seg * XH, sF + (q * HR + r) * LD + seg * XH, qg == 0, tap,
-                          sH + (q * HR + r) * LDH + seg * XH);
+          fir_row<SB, XH, decltype(tap), OFF>(sB + r * LD + seg * XH,
+                                              sF + (q * HR + r) * LD + seg * XH, qg == 0, tap,
+                                              sH + (q * HR + r) * LDH + seg * XH);
       }
       for (int hk = tid; hk < 2 * (T - FULL); hk += NT) {
         int q, r, seg;
@@ -290,11 +319,11 @@ filter_tile_kernel(const FilterArgs a, const Taps taps) {
         if (qg > n) continue;
         const int x = seg * XH + (hk & 1) * (XH / 2);
         if constexpr (BOX)
-          box_row<SB, XH / 2>(sB + r * LD + x, sF + (q * HR + r) * LD + x, qg == 0, a.S,
-                              sH + (q * HR + r) * LDH + x);
+          box_row<SB, XH / 2, OFF>(sB + r * LD + x, sF + (q * HR + r) * LD + x, qg == 0, a.S,
+                                   sH + (q * HR + r) * LDH + x);
         else
-          fir_row<SB, XH / 2>(sB + r * LD + x, sF + (q * HR + r) * LD + x, qg == 0, tap,
-                              sH + (q * HR + r) * LDH + x);
+          fir_row<SB, XH / 2, decltype(tap), OFF>(sB + r * LD + x, sF + (q * HR + r) * LD + x,
+                                                  qg == 0, tap, sH + (q * HR + r) * LDH + x);
       }
     }
     __syncthreads();

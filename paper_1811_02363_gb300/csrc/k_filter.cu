@@ -2,6 +2,7 @@
 // the guard fix-up, and the dispatch of the fused convolution/combine tile
 // kernel (filter_tile.cuh) for hdf_apply.
 #include <math.h>
+#include <stdint.h>
 
 #include "combine.cuh"
 #include "filter_tile.cuh"
@@ -106,7 +107,8 @@ cudaError_t launch_filter(hdf_handle* h, const float* f, float* g, cudaStream_t 
   cudaError_t e = cudaMemsetAsync(h->ctrl + CTRL_FALLBACK, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   FilterArgs a{f, h->B, h->C, g, h->den, h->rmax, h->ctrl, d.H, d.W, d.n,
-               d.spatial == HDF_SPATIAL_BOX ? 1 : 0, d.S};
+               d.spatial == HDF_SPATIAL_BOX ? 1 : 0, d.S,
+               (d.W % 4 == 0 && reinterpret_cast<uintptr_t>(f) % 16 == 0) ? 1 : 0};
   e = launch_filter_sb(SB, P, a, taps, st);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;

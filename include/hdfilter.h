@@ -209,7 +209,9 @@ hdf_status hdf_bruteforce(const hdf_desc* desc, const float* d_f, const void* d_
  * distance and farthest-point pass, 4 root node, 5 Lloyd iteration, 6
  * partition count, 7 partition scatter, 8 children written; between them:
  * 9 end of block 0's Lloyd pass, 11 Lloyd state reloaded, 12-14 block 0
- * finishing a split (all partial sums arrived, reduced, update published).
+ * finishing a split (all partial sums arrived, reduced, update published),
+ * 15 round set-up done, 16 end of block 0's distance pass.
+ * paper_1811_02363_gb300.cluster_trace prints the per-phase breakdown.
  * h_events: host, room for 2*cap int64.  *count = events written.
  * Synchronises `stream`.  Tracing support; not part of the paper's method. */
 hdf_status hdf_get_trace(hdf_handle* h, int64_t* h_events, int cap, int* count, void* stream);

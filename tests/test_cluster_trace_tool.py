@@ -1,0 +1,16 @@
+"""The phase names of the clustering trace tool cover exactly the phase ids
+the clustering kernel records (the TracePhase enum of its argument header)."""
+import os
+import re
+
+from paper_1811_02363_gb300 import cluster_trace
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_phase_ids_match_the_kernel_enum():
+    src = open(os.path.join(ROOT, "paper_1811_02363_gb300", "csrc", "cluster_args.cuh")).read()
+    enum = src[src.index("enum TracePhase"):]
+    enum = enum[:enum.index("};")]
+    ids = {int(v): k[3:] for k, v in re.findall(r"(TR_\w+)\s*=\s*(\d+)", enum)}
+    assert ids == cluster_trace.PHASES

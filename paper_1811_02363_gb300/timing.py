@@ -1,0 +1,83 @@
+"""Stage timings of the named synthetic workloads on the current GPU.
+
+For each workload: the PCA guide (nonlocal means), the clustering, the filter
+apply with the Gaussian, box and recursive-Gaussian spatial kernels, and with
+--backward the gradient pass (dL/df, dL/dlog sigma_s, dL/dlog sigma_r) of the
+Gaussian filter for a random upstream gradient.  Times are medians of CUDA
+events on the current stream, inputs resident on the device.
+
+    python -m paper_1811_02363_gb300.timing hyper512 color2048 --backward
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+
+import numpy as np
+import torch
+
+from . import api, synthetic
+
+WORKLOADS = ["color256", "hyper512", "nlm1024", "color2048"]
+
+
+def median_ms(fn, reps: int = 10) -> float:
+    s = torch.cuda.current_stream()
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        fn()
+        b.record(s)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
+
+
+def workload_times(name: str, backward: bool = False) -> dict:
+    w = synthetic.workload(name)
+    f = torch.from_numpy(w["f"]).cuda()
+    n, H, W = f.shape
+    nlm = name == "nlm1024"
+    rho = w["pca_dims"] if nlm else n
+    out = {"workload": name, "pixels": H * W, "K": w["K"], "sigma_s": w["sigma_s"],
+           "sigma_r": w["sigma_r"]}
+    g = torch.empty_like(f)
+    centres = None
+    for spatial in ("gauss", "box", "young"):
+        flt = api.HDFilter(H, W, n, rho, w["K"], w["sigma_s"], w["sigma_r"], spatial=spatial)
+        try:
+            p = flt.nlm_guide(f, w["patch"]) if nlm else f
+            if spatial == "gauss":
+                if nlm:
+                    out["guide_ms"] = median_ms(lambda: flt.nlm_guide(f, w["patch"], out=p))
+                out["S"] = int(math.ceil(3.0 * w["sigma_s"]))
+                out["cluster_ms"] = median_ms(lambda: flt.cluster(p))
+                centres = flt.get_centers()
+            else:
+                flt.set_centers(centres)
+            out[f"apply_{spatial}_ms"] = median_ms(lambda: flt.apply(f, p, g))
+            if backward and spatial == "gauss":
+                G = torch.randn(f.shape, device=f.device, dtype=f.dtype,
+                                generator=torch.Generator(device=f.device).manual_seed(5))
+                out["backward_ms"] = median_ms(lambda: flt.backward(f, p, G))
+            out[f"stats_{spatial}"] = flt.stats()
+        finally:
+            flt.close()
+    return out
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("workloads", nargs="*", default=WORKLOADS, choices=WORKLOADS)
+    ap.add_argument("--backward", action="store_true", help="also time the gradient pass")
+    args = ap.parse_args()
+    for name in args.workloads:
+        print(json.dumps(workload_times(name, args.backward)), flush=True)
+
+
+if __name__ == "__main__":
+    main()

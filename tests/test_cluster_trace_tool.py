@@ -14,3 +14,10 @@ def test_phase_ids_match_the_kernel_enum():
     enum = enum[:enum.index("};")]
     ids = {int(v): k[3:] for k, v in re.findall(r"(TR_\w+)\s*=\s*(\d+)", enum)}
     assert ids == cluster_trace.PHASES
+
+
+def test_timing_tool_names_the_synthetic_workloads():
+    from paper_1811_02363_gb300 import synthetic, timing
+    for name in timing.WORKLOADS:
+        w = synthetic.workload(name)
+        assert {"f", "K", "sigma_s", "sigma_r"} <= set(w)

@@ -70,11 +70,21 @@ def workload_times(name: str, backward: bool = False) -> dict:
     return out
 
 
-def main() -> None:
+def parse_args(argv=None) -> argparse.Namespace:
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("workloads", nargs="*", default=WORKLOADS, choices=WORKLOADS)
+    ap.add_argument("workloads", nargs="*", metavar="workload",
+                    help=f"one or more of {', '.join(WORKLOADS)} (default: all)")
     ap.add_argument("--backward", action="store_true", help="also time the gradient pass")
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
+    bad = [w for w in args.workloads if w not in WORKLOADS]
+    if bad:
+        ap.error(f"unknown workload(s) {bad}; choose from {WORKLOADS}")
+    args.workloads = args.workloads or list(WORKLOADS)
+    return args
+
+
+def main() -> None:
+    args = parse_args()
     for name in args.workloads:
         print(json.dumps(workload_times(name, args.backward)), flush=True)
 

@@ -21,3 +21,10 @@ def test_timing_tool_names_the_synthetic_workloads():
     for name in timing.WORKLOADS:
         w = synthetic.workload(name)
         assert {"f", "K", "sigma_s", "sigma_r"} <= set(w)
+
+
+def test_timing_tool_arguments():
+    from paper_1811_02363_gb300 import timing
+    assert timing.parse_args([]).workloads == timing.WORKLOADS
+    a = timing.parse_args(["color2048", "--backward"])
+    assert a.workloads == ["color2048"] and a.backward

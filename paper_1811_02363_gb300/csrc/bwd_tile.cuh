@@ -39,6 +39,7 @@ struct BwdArgs {
   double* part;          // MODE_GAMMA out: per-CTA log sigma_s partial
   const int* ctrl;
   int H, W, n;
+  int vec;               // W % 4 == 0 and f 16-byte aligned: 16-byte halo staging
 };
 
 template <int SB, int MODE, int TY_>
@@ -46,14 +47,21 @@ struct BwdCfg {
   static constexpr int TX = 32, TY = TY_, P = 2, NT = 512;
   static constexpr int YV = TX * TY * P / NT;          // 8 (TY 64) or 4 (TY 32)
   static constexpr int XH = 16, NSEG = TX / XH;
-  static constexpr int NIN = XH + 2 * SB, NIN4 = (NIN + 3) / 4;
-  static constexpr int HR = TY + 2 * SB, HC = TX + 2 * SB;
-  static constexpr int LD = round_ld((NSEG - 1) * XH + 4 * NIN4);
+  static constexpr int SA = (SB + 3) & ~3, OFF = SA - SB;   // aligned staging start x0 - SA
+  static constexpr int NIN = XH + 2 * SB + OFF, NIN4 = (NIN + 3) / 4;
+  static constexpr int HR = TY + 2 * SB, HC = TX + 2 * SA;
+  // row stride: >= the staged columns and the row pass's 16-byte loads, and
+  // = 4 (mod 8) words, so that the 16-byte loads of 8 consecutive tasks (rows
+  // r .. r + 3, two segments each) fall in distinct bank quads
+  static constexpr int NEED = (NSEG - 1) * XH + 4 * NIN4 > HC ? (NSEG - 1) * XH + 4 * NIN4 : HC;
+  static constexpr int LD = ((NEED + 3) / 8) * 8 + 4;
   static constexpr int LDH = round_ld(TX);
   static constexpr int NH = MODE == MODE_GAMMA ? 2 : 1;  // row-pass outputs per plane
   static constexpr int SF = P * HR * LD, SBF = HR * LD, SH = NH * P * HR * LDH, SRED = P * TY * TX;
   static constexpr size_t SMEM = sizeof(float) * (size_t)(SF + 2 * SBF + SH + SRED);
   static_assert(TX * (TY / YV) * P == NT, "one column run per thread");
+  static_assert(LD >= HC, "row stride must hold the staged columns");
+  static_assert(SMEM <= 232448, "shared memory per block");
 };
 
 template <int SB, int MODE, int TY_>
@@ -63,6 +71,7 @@ bwd_tile_kernel(const BwdArgs a, const Taps taps, const Taps taps2) {
   constexpr int TX = Cfg::TX, TY = Cfg::TY, P = Cfg::P, NT = Cfg::NT, YV = Cfg::YV;
   constexpr int XH = Cfg::XH, NSEG = Cfg::NSEG, HR = Cfg::HR, HC = Cfg::HC, LD = Cfg::LD;
   constexpr int LDH = Cfg::LDH, NIN4 = Cfg::NIN4, NTAP = 2 * SB + 1;
+  constexpr int SA = Cfg::SA, OFF = Cfg::OFF, CPR = HC / 4;
   extern __shared__ __align__(16) float sm[];
   float* sF = sm;                              // [P][HR][LD] f (GAMMA) or lambda (ADJ)
   float* sB0 = sF + Cfg::SF;                   // [2][HR][LD] b_k (GAMMA) or c_k (ADJ)
@@ -85,20 +94,36 @@ bwd_tile_kernel(const BwdArgs a, const Taps taps, const Taps taps2) {
   unsigned col_ok = 0;                  // bit j: column lane + 32 j inside the image
 #pragma unroll
   for (int j = 0; j < CPL; ++j) {
-    const int c = lane + 32 * j, xx = x0 - SB + c;
+    const int c = lane + 32 * j, xx = x0 - SA + c;
     if (c < HC && xx >= 0 && xx < W) col_ok |= 1u << j;
   }
+  const bool vec = a.vec != 0;
   double sig = 0.0;                                   // GAMMA: log sigma_s partial
 
   for (int chunk = 0; chunk < nchunks; ++chunk) {
     const int qgv = chunk * P + qv;
     // ---- stage the chunk's planes (image channels, or lambda planes) and the
-    // per-k plane: a warp copies whole halo rows, lanes over the columns
+    // per-k plane, columns x0 - SA .. x0 + TX + SA - 1: 16-byte copies when
+    // the image allows (a chunk is then wholly inside or outside it), else a
+    // warp per halo row, lanes over the columns; the row pass reads from
+    // column OFF = SA - SB on
     auto stage_rows = [&](const float* plane, float* dst) {
+      if (vec) {
+        constexpr int RPW = (HR + NT / 32 - 1) / (NT / 32);
+        for (int i = lane; i < RPW * CPR; i += 32) {
+          const int rl = i / CPR, ch = i - rl * CPR;
+          const int r = warp + rl * (NT / 32);
+          if (r >= HR) continue;
+          const int yy = y0 - SB + r, xx = x0 - SA + 4 * ch;
+          const bool ok = yy >= 0 && yy < H && xx >= 0 && xx + 4 <= W;
+          cp_async16(dst + r * LD + 4 * ch, ok ? plane + (size_t)yy * W + xx : plane, ok);
+        }
+        return;
+      }
       for (int r = warp; r < HR; r += NT / 32) {
         const int yy = y0 - SB + r;
         const bool rok = yy >= 0 && yy < H;
-        const float* grow = plane + (ptrdiff_t)yy * W + (x0 - SB);
+        const float* grow = plane + (ptrdiff_t)yy * W + (x0 - SA);
         float* srow = dst + r * LD;
 #pragma unroll
         for (int j = 0; j < CPL; ++j) {
@@ -158,18 +183,21 @@ bwd_tile_kernel(const BwdArgs a, const Taps taps, const Taps taps2) {
         const float4* pb = reinterpret_cast<const float4*>(sB + r * LD + seg * XH);
         const float4* pf = reinterpret_cast<const float4*>(sF + (q * HR + r) * LD + seg * XH);
         const bool plain = (MODE == MODE_GAMMA && qg == 0);   // U_0 = b_k
-        float in[4 * NIN4];
+        float raw[4 * NIN4];
 #pragma unroll
         for (int t = 0; t < NIN4; ++t) {
           const float4 b = pb[t];
           if (plain) {
-            in[4 * t] = b.x; in[4 * t + 1] = b.y; in[4 * t + 2] = b.z; in[4 * t + 3] = b.w;
+            raw[4 * t] = b.x; raw[4 * t + 1] = b.y; raw[4 * t + 2] = b.z; raw[4 * t + 3] = b.w;
           } else {
             const float4 v = pf[t];
-            in[4 * t] = b.x * v.x; in[4 * t + 1] = b.y * v.y;
-            in[4 * t + 2] = b.z * v.z; in[4 * t + 3] = b.w * v.w;
+            raw[4 * t] = b.x * v.x; raw[4 * t + 1] = b.y * v.y;
+            raw[4 * t + 2] = b.z * v.z; raw[4 * t + 3] = b.w * v.w;
           }
         }
+        float in[XH + 2 * SB];
+#pragma unroll
+        for (int i = 0; i < XH + 2 * SB; ++i) in[i] = raw[i + OFF];
         float h[XH];
 #pragma unroll
         for (int o = 0; o < XH; ++o) h[o] = 0.0f;

@@ -19,6 +19,7 @@
 //      - eta . (dA c) with dA_kl = A_kl |mu_k - mu_l|^2 / sigma_r^2;
 //   7. FP64 sums of the per-block scalar partials.
 #include <math.h>
+#include <stdint.h>
 
 #include "bwd_tile.cuh"
 #include "hdf_internal.cuh"
@@ -243,7 +244,8 @@ cudaError_t launch_backward(hdf_handle* h, const float* f, const void* p, const 
     t2.w[SB + j] = (float)((double)exact.w[d.S + j] * j * j / (d.sigma_s * d.sigma_s));
   }
   BwdArgs a{f, h->bw_lam, h->B, h->C, h->bw_gam, h->bw_bet, grad_f,
-            h->grad_scratch + PART_SIGMA_S, h->ctrl, d.H, d.W, d.n};
+            h->grad_scratch + PART_SIGMA_S, h->ctrl, d.H, d.W, d.n,
+            (d.W % 4 == 0 && reinterpret_cast<uintptr_t>(f) % 16 == 0) ? 1 : 0};
   if ((e = launch_bwd_sb(SB, MODE_GAMMA, a, t1, t2, st)) != cudaSuccess) return e;
   if ((e = launch_bwd_sb(SB, MODE_ADJ, a, t1, t2, st)) != cudaSuccess) return e;
   // 6. per-pixel closing terms

@@ -89,3 +89,25 @@ def test_autograd_function(api):
     assert torch.equal(fd.grad, gf2)
     assert float(ls.grad) == pytest.approx(float(gls2), rel=1e-6)
     assert float(lr.grad) == pytest.approx(float(glr2), rel=1e-6)
+
+
+@pytest.mark.parametrize("ss", [1.3, 5.0, 8.0])
+def test_backward_word_and_vector_staging_agree(api, ss):
+    """The backward tile kernels stage halo rows by 16-byte copies when
+    W % 4 == 0 and the image is 16-byte aligned, by single words otherwise;
+    an image stored one float past an aligned address takes the word path and
+    must give the same gradients bit for bit."""
+    f = synthetic.color_rectangles(44, 48, seed=92)
+    mu = O.bisecting_kmeans(f.reshape(3, -1).T.astype(np.float64), 6)[0].astype(np.float32)
+    flt = api.HDFilter(44, 48, 3, 3, 6, ss, 0.3)
+    flt.set_centers(mu)
+    fa = torch.from_numpy(f).cuda()
+    buf = torch.empty(fa.numel() + 1, device="cuda", dtype=torch.float32)
+    fm = buf[1:].view(3, 44, 48)
+    fm.copy_(fa)
+    assert fm.data_ptr() % 16 != 0 and fa.data_ptr() % 16 == 0
+    G = torch.from_numpy(np.random.default_rng(93).normal(size=f.shape).astype(np.float32)).cuda()
+    ga, sa, ra = flt.backward(fa, fa, G)
+    gm, sm, rm = flt.backward(fm, fm, G)
+    assert torch.equal(ga, gm)
+    assert float(sa) == float(sm) and float(ra) == float(rm)

@@ -1133,17 +1133,26 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
         if (recompute) {
           // accepted sums, the new means (a, b) and the distance each centre moved
           const double nb_cnt = (double)sl.cnt_b_cur, na_cnt = (double)(sl.count - sl.cnt_b_cur);
-          double ma2 = 0.0, mb2 = 0.0, na = 0.0, nb = 0.0;
+          // The centres in FP64; the norms behind the skip bounds in FP32 (FP64
+          // issues at a small fraction of the FP32 rate).  Rounded up: the
+          // FP32 sums of <= 2 rho nonnegative terms and the square roots are
+          // within 2^-19 relative, covered by the factor 1 + 2^-16; squares
+          // that underflow lose less than 1e-18 in a norm, covered by the
+          // absolute 1e-18.  Upper bounds only decide which points are
+          // re-examined, never an assignment.
+          float ma2 = 0.0f, mb2 = 0.0f, na = 0.0f, nb = 0.0f;
           for (int d = lane; d < rho; d += 32) {
             const double sb = fin[d] + (it > 0 ? acc_sum[i * rho + d] : 0.0);
             acc_sum[i * rho + d] = sb;
             const double mb = quotient(sb, nb_cnt);
             const double ma = quotient(nsum[i * rho + d] - sb, na_cnt);
-            const double ua = ma - c64[(2 * i) * rho + d], ub = mb - c64[(2 * i + 1) * rho + d];
-            ma2 += ua * ua;
-            mb2 += ub * ub;
-            na += ma * ma;
-            nb += mb * mb;
+            const float ua = (float)(ma - c64[(2 * i) * rho + d]);
+            const float ub = (float)(mb - c64[(2 * i + 1) * rho + d]);
+            const float fa = (float)ma, fb = (float)mb;
+            ma2 = fmaf(ua, ua, ma2);
+            mb2 = fmaf(ub, ub, mb2);
+            na = fmaf(fa, fa, na);
+            nb = fmaf(fb, fb, nb);
             c64[(2 * i) * rho + d] = ma;
             c64[(2 * i + 1) * rho + d] = mb;
           }
@@ -1155,9 +1164,10 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
             nb += __shfl_xor_sync(0xffffffffu, nb, o);
           }
           if (lane == 0) {
-            s.slack[i] = (float)((sqrt_up(ma2) + sqrt_up(mb2)) * ROUND_UP) + 1e-30f;
+            constexpr float UP32 = 1.0f + 1.0f / 65536.0f;
+            s.slack[i] = (sqrtf(ma2) + sqrtf(mb2)) * UP32 + 1e-18f;
             s.cum[i] = (s.cum[i] + (double)s.slack[i]) * ROUND_UP;
-            s.cabs[i] = (float)((sqrt_up(na) + sqrt_up(nb)) * (1.0 / 1048576.0));
+            s.cabs[i] = (sqrtf(na) + sqrtf(nb)) * (UP32 / 1048576.0f);
             sl.cnt_b_acc = sl.cnt_b_cur;
           }
         }

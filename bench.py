@@ -384,7 +384,7 @@ def run_gpu(args) -> None:
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak_tflops = 152 * 128 * 2 * sm_max * 1e6 / 1e12
     npx = H * W
-    # Clustering: SURVEY-style model of plain Lloyd traffic, rho*4 B per point
+    # Clustering: a model of plain Lloyd traffic, rho*4 B per point
     # per assignment pass, 20 passes per level, log2 K levels.
     cl_bytes = npx * 31 * 4 * 20 * 5
     cl_s = statistics.median(cluster_ms) * 1e-3

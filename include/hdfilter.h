@@ -52,7 +52,7 @@ typedef enum {
   HDF_ECUDA = 3,         /* a CUDA runtime call failed (see hdf_last_cuda_error) */
   HDF_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
   HDF_EDOMAIN = 5,       /* non-finite value met where the method needs finite data */
-  HDF_EUNSUPPORTED = 6   /* valid request this build does not handle (e.g. S > 32) */
+  HDF_EUNSUPPORTED = 6   /* valid request the library does not handle (e.g. S > 32) */
 } hdf_status;
 
 enum { HDF_GUIDE_F32 = 0, HDF_GUIDE_BF16 = 1 };
@@ -70,7 +70,7 @@ enum { HDF_SPATIAL_GAUSS = 0,   /* omega(j) = exp(-|j|^2 / 2 sigma_s^2) on W (Se
                                    HDF_EUNSUPPORTED; hdf_bruteforce computes the exact
                                    Gaussian it approximates */ };
 
-/* Limits of this build. */
+/* Limits of the library. */
 #define HDF_MAX_K 64           /* clusters */
 #define HDF_MAX_RHO 64         /* guide dimensions */
 #define HDF_MAX_S 32           /* window half-width */

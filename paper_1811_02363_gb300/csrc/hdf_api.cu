@@ -77,7 +77,7 @@ const char* hdf_status_string(hdf_status s) {
     case HDF_ECUDA: return "HDF_ECUDA: CUDA runtime error";
     case HDF_ETIMEOUT: return "HDF_ETIMEOUT: bounded device wait gave up";
     case HDF_EDOMAIN: return "HDF_EDOMAIN: input outside the method's domain";
-    case HDF_EUNSUPPORTED: return "HDF_EUNSUPPORTED: beyond this build's limits";
+    case HDF_EUNSUPPORTED: return "HDF_EUNSUPPORTED: beyond the library's limits";
   }
   return "unknown hdf_status";
 }

@@ -182,7 +182,13 @@ class ClockSampler:
             self.proc.kill()
             self.proc.wait()
         self.thread.join(timeout=5)
-        out = "".join(self.lines[self.n0:] or self.lines)
+        return self.summarize(self.lines[self.n0:] or self.lines)
+
+    @staticmethod
+    def summarize(lines) -> dict:
+        """Median SM clock, maximum clock and the throttle reasons seen, from
+        nvidia-smi CSV lines (no header, no units) of FIELDS."""
+        out = "".join(lines)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in out.strip().splitlines():

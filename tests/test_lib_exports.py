@@ -59,6 +59,32 @@ def test_argument_errors_without_device_work(L):
     assert lib.hdf_status_string(L.HDF_ETIMEOUT).startswith(b"HDF_ETIMEOUT")
 
 
+@pytest.mark.parametrize("field,value,status", [
+    ("W", 0, "HDF_EINVAL"), ("n", 0, "HDF_EINVAL"), ("rho", 0, "HDF_EINVAL"),
+    ("K", 0, "HDF_EINVAL"), ("sigma_s", 0.0, "HDF_EINVAL"), ("sigma_s", float("nan"), "HDF_EINVAL"),
+    ("sigma_r", float("inf"), "HDF_EINVAL"), ("S", -1, "HDF_EINVAL"), ("guide_dtype", 2, "HDF_EINVAL"),
+    ("coef", 2, "HDF_EINVAL"), ("rho", 10 ** 6, "HDF_EUNSUPPORTED"), ("n", 10 ** 6, "HDF_EUNSUPPORTED"),
+    ("H", 1 << 20, "HDF_EUNSUPPORTED"),   # H * W beyond the pixel limit
+])
+def test_each_invalid_field_is_reported(L, field, value, status):
+    lib = L.lib()
+    d = L.hdf_desc(H=8, W=1 << 12, n=3, rho=3, K=4, S=0, sigma_s=1.0, sigma_r=0.1,
+                   guide_dtype=0, coef=0)
+    setattr(d, field, value)
+    h = C.c_void_p()
+    assert lib.hdf_create(C.byref(h), C.byref(d)) == getattr(L, status)
+    assert lib.hdf_bruteforce(C.byref(d), None, None, None, None) in (L.HDF_EINVAL,
+                                                                     getattr(L, status))
+
+
+def test_recursive_gaussian_needs_sigma_half(L):
+    lib = L.lib()
+    d = L.hdf_desc(H=8, W=8, n=3, rho=3, K=4, S=0, sigma_s=0.4, sigma_r=0.1,
+                   guide_dtype=0, coef=0, spatial=L.HDF_SPATIAL_YOUNG)
+    h = C.c_void_p()
+    assert lib.hdf_create(C.byref(h), C.byref(d)) == L.HDF_EINVAL
+
+
 def test_batch_argument_errors_without_device_work(L):
     lib = L.lib()
     d = (L.hdf_desc * 2)()

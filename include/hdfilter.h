@@ -164,14 +164,17 @@ hdf_status hdf_backward(hdf_handle* h, const float* d_f, const void* d_p,
                         const float* d_grad_g, float* d_grad_f,
                         double* d_grad_log_sigma, void* stream);
 
-/* hdf_apply for callers that cannot allocate device memory (code being
- * captured into a CUDA graph, frameworks that own all device memory through
- * their own pool, latency-critical paths where cudaMalloc/cudaFree would
- * stall).  Same result as hdf_create + hdf_set_centers + hdf_apply, but no
- * handle: the scratch it needs lives in one 32 MiB static device array that
- * the library holds on every GPU where it is loaded, until the process exits.
+/* hdf_apply for callers that cannot allocate device memory: a framework or
+ * plug-in host that owns all device memory through its own pool and forbids
+ * foreign allocations, or a latency-critical path where a cudaMalloc/cudaFree
+ * pair (which can synchronise the device) would stall.  Same result as
+ * hdf_create + hdf_set_centers + hdf_apply, but no handle: the scratch it
+ * needs lives in one 32 MiB static device array that the library holds on
+ * every GPU where it is loaded, until the process exits.
  * The paper has no counterpart of this call.
- *   desc: filter description (desc->K is ignored; K is the argument).
+ *   desc: filter description (desc->K is ignored; K is the argument);
+ *         checked exactly as hdf_create checks it (HDF_EINVAL /
+ *         HDF_EUNSUPPORTED before anything is enqueued).
  *   d_mu: device float32 centres, K x rho row-major (caller-owned, read only).
  *   d_f, d_p, d_g: as in hdf_apply.
  * A call needs about K*K*12 + H*W*(8*K + 13) bytes of that array; larger
@@ -182,7 +185,9 @@ hdf_status hdf_backward(hdf_handle* h, const float* d_f, const void* d_p,
  * make that first call before any stream capture.  All calls share the
  * array and it keeps the last call's contents: calls whose GPU work overlaps
  * (other streams, other host threads) race on it and must be serialised.
- * Asynchronous on `stream`. */
+ * No device-side status is reported (the guard count of Eq. (15)-(16), a
+ * truncated pseudo-inverse of A): there is no handle to read it from.
+ * HDF_SPATIAL_YOUNG returns HDF_EUNSUPPORTED.  Asynchronous on `stream`. */
 hdf_status hdf_apply_static(const hdf_desc* desc, const float* d_mu, int K, const float* d_f,
                             const void* d_p, float* d_g, void* stream);
 

@@ -27,7 +27,12 @@ hdf_status check_desc(hdf_desc* d) {
       !isfinite(d->sigma_r))
     return HDF_EINVAL;
   if (d->S < 0) return HDF_EINVAL;
-  if (d->S == 0) d->S = (int)ceil(3.0 * d->sigma_s);
+  if (d->S == 0) {
+    // S = ceil(3 sigma_s), decided before the conversion to int so that a
+    // huge sigma_s cannot overflow it
+    if (3.0 * d->sigma_s > (double)HDF_MAX_S) return HDF_EUNSUPPORTED;
+    d->S = (int)ceil(3.0 * d->sigma_s);
+  }
   if (d->guide_dtype != HDF_GUIDE_F32 && d->guide_dtype != HDF_GUIDE_BF16) return HDF_EINVAL;
   if (d->coef != HDF_COEF_OPT && d->coef != HDF_COEF_INDICATOR) return HDF_EINVAL;
   if (d->spatial != HDF_SPATIAL_GAUSS && d->spatial != HDF_SPATIAL_BOX &&

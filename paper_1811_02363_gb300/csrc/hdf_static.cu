@@ -6,17 +6,18 @@
 // buffers; the caller passes only the inputs and the output.
 //
 // Who needs this: code that runs where an allocation is not allowed or not
-// acceptable -- for example inside a region that is being captured into a
-// CUDA graph (cudaMalloc would break the capture), inside a framework that
-// owns all device memory through its own pool and forbids foreign
-// allocations, or on a latency-critical path where a cudaMalloc/cudaFree
-// pair (which can synchronise the device) is too slow.
+// acceptable -- a framework or plug-in host that owns all device memory
+// through its own pool and forbids foreign allocations, or a latency-critical
+// path where a cudaMalloc/cudaFree pair (which can synchronise the device) is
+// too slow.
 //
 // The array is part of the library's device image: every GPU on which the
 // library's kernels are loaded holds it until the process exits.  Calls
 // share it and it keeps the previous call's contents, so calls whose work
 // overlaps on the GPU (concurrent streams, several host threads) race on
-// it and must be serialised by the caller.
+// it and must be serialised by the caller.  The call reports no device-side
+// status (guard pixels, a truncated pseudo-inverse): there is no handle to
+// read it from.
 #include <math.h>
 #include <string.h>
 
@@ -54,19 +55,6 @@ cudaError_t scratch_address(int dev, void** out) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-hdf_status validate(hdf_desc* d, int K) {
-  if (d->H < 1 || d->W < 1 || d->n < 1 || d->rho < 1 || K < 1) return HDF_EINVAL;
-  if (!(d->sigma_s > 0.0) || !(d->sigma_r > 0.0)) return HDF_EINVAL;
-  if (d->S < 0) return HDF_EINVAL;
-  if (d->S == 0) d->S = (int)ceil(3.0 * d->sigma_s);
-  if (d->guide_dtype != HDF_GUIDE_F32 && d->guide_dtype != HDF_GUIDE_BF16) return HDF_EINVAL;
-  if (d->coef != HDF_COEF_OPT && d->coef != HDF_COEF_INDICATOR) return HDF_EINVAL;
-  if (K > HDF_MAX_K || d->rho > HDF_MAX_RHO || d->S > HDF_MAX_S || d->n > HDF_MAX_N)
-    return HDF_EUNSUPPORTED;
-  if ((long long)d->H * d->W >= (1LL << 31)) return HDF_EUNSUPPORTED;
-  return HDF_OK;
-}
-
 }  // namespace
 
 extern "C" hdf_status hdf_apply_static(const hdf_desc* desc, const float* d_mu, int K,
@@ -75,10 +63,10 @@ extern "C" hdf_status hdf_apply_static(const hdf_desc* desc, const float* d_mu, 
   if (!desc || !d_mu || !d_f || !d_p || !d_g) return HDF_EINVAL;
   if ((const void*)d_g == (const void*)d_f || (const void*)d_g == d_p) return HDF_EINVAL;
   hdf_desc d = *desc;
-  hdf_status st = validate(&d, K);
+  d.K = K;
+  hdf_status st = hdf::check_desc(&d);   // the same checks as hdf_create
   if (st != HDF_OK) return st;
   if (d.spatial == HDF_SPATIAL_YOUNG) return HDF_EUNSUPPORTED;   // needs per-plane scratch
-  d.K = K;
   const size_t N = (size_t)d.H * d.W;
 
   // carve the scratch: control words, A^+ (f64, f32), B, C, s, den, rmax, guard list
@@ -95,9 +83,10 @@ extern "C" hdf_status hdf_apply_static(const hdf_desc* desc, const float* d_mu, 
   if (off > kStaticScratchBytes) return HDF_EUNSUPPORTED;   // beyond the 32 MiB array
 
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HDF_ECUDA;
+  HDF_CUDA(cudaGetDevice(&dev), "apply_static cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return HDF_EUNSUPPORTED;
   void* base = nullptr;
-  if (scratch_address(dev, &base) != cudaSuccess) return HDF_ECUDA;
+  HDF_CUDA(scratch_address(dev, &base), "apply_static cudaGetSymbolAddress");
   unsigned char* w = (unsigned char*)base;
   cudaStream_t st_ = (cudaStream_t)stream;
 
@@ -121,10 +110,10 @@ extern "C" hdf_status hdf_apply_static(const hdf_desc* desc, const float* d_mu, 
 
   // The previous call's contents stay in the array: clear the control words
   // (error, guard counter), then set K_eff.
-  if (cudaMemsetAsync(h.ctrl, 0, sizeof(int) * hdf::CTRL_WORDS, st_) != cudaSuccess) return HDF_ECUDA;
-  if (hdf::launch_set_int(h.ctrl + hdf::CTRL_K_EFF, K, st_) != cudaSuccess) return HDF_ECUDA;
-  if (hdf::launch_fit(&h, st_) != cudaSuccess) return HDF_ECUDA;
-  if (hdf::launch_rangemap(&h, d_p, st_) != cudaSuccess) return HDF_ECUDA;
-  if (hdf::launch_filter(&h, d_f, d_g, st_) != cudaSuccess) return HDF_ECUDA;
+  HDF_CUDA(cudaMemsetAsync(h.ctrl, 0, sizeof(int) * hdf::CTRL_WORDS, st_), "apply_static clear");
+  HDF_CUDA(hdf::launch_set_int(h.ctrl + hdf::CTRL_K_EFF, K, st_), "apply_static K");
+  HDF_CUDA(hdf::launch_fit(&h, st_), "apply_static fit");
+  HDF_CUDA(hdf::launch_rangemap(&h, d_p, st_), "apply_static rangemap");
+  HDF_CUDA(hdf::launch_filter(&h, d_f, d_g, st_), "apply_static filter");
   return HDF_OK;
 }

@@ -104,3 +104,28 @@ def test_batch_argument_errors_without_device_work(L):
     assert lib.hdf_batch_tune(None, 3, None) == L.HDF_EINVAL
     assert lib.hdf_batch_get_info(None, None) == L.HDF_EINVAL
 
+
+
+@pytest.mark.parametrize("field,value,status", [
+    ("sigma_s", float("inf"), "HDF_EINVAL"),
+    ("sigma_s", 1e10, "HDF_EUNSUPPORTED"),     # S = ceil(3 sigma_s) would not fit HDF_MAX_S
+    ("sigma_s", 11.0, "HDF_EUNSUPPORTED"),     # S = 33
+    ("spatial", 7, "HDF_EINVAL"),
+])
+def test_sigma_and_spatial_checks_before_any_work(L, field, value, status):
+    """hdf_create and hdf_apply_static share one descriptor check: an infinite
+    or huge sigma_s and an unknown spatial kernel are refused before anything
+    is allocated or enqueued."""
+    import torch
+    lib = L.lib()
+    d = L.hdf_desc(H=8, W=8, n=3, rho=3, K=4, S=0, sigma_s=1.0, sigma_r=0.1,
+                   guide_dtype=0, coef=0)
+    setattr(d, field, value)
+    h = C.c_void_p()
+    assert lib.hdf_create(C.byref(h), C.byref(d)) == getattr(L, status)
+    if torch.cuda.is_available():
+        return   # the static call below passes placeholder pointers: host without a GPU only
+    dummy = C.c_void_p(256)
+    out = C.c_void_p(512)
+    assert lib.hdf_apply_static(C.byref(d), dummy, 4, dummy, dummy, out, None) == \
+        getattr(L, status)

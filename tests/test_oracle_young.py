@@ -1,8 +1,10 @@
 """Pins of the oracle's Young recursive Gaussian (the O(1) Gaussian
 convolution Sec. II-C names): the library recursion against a literal loop,
 unit gain, symmetry and closeness of the impulse response to a normalised
-Gaussian, separability (rows and columns commute), and Algorithm 1 with it
-reducing to the normalised recursive blur when sigma_r is huge.  CPU only."""
+Gaussian, separability (rows and columns commute), Algorithm 1 with it
+reducing to the normalised recursive blur when sigma_r is huge, the
+coefficients against Young and van Vliet's published pole positions, and the
+impulse response's variance against its closed form.  CPU only."""
 import math
 
 import numpy as np
@@ -85,3 +87,61 @@ def test_planted_sign_error_is_caught():
     w = lfilter([B], [1.0, a1, a2, a3], x)
     wrong = np.flip(lfilter([B], [1.0, a1, a2, a3], np.flip(w)))
     assert np.max(np.abs(wrong - _loop(x, 3.0))) > 1e-2
+
+
+# Young and van Vliet (1995) derive their recursion from the three poles of a
+# rational approximation of the Gaussian's transfer function, at
+# m0 = 1.16680 (real) and m1 +- i m2 = 1.10783 +- 1.40586 i, scaled by q: the
+# causal pass has poles z = q / (m0 + q) and q / (m1 + q -+ i m2), i.e. its
+# denominator is (m0 + q - q z^-1) ((m1 + q - q z^-1)^2 + m2^2) up to a
+# constant factor.  Those pole positions are published numbers independent of
+# the polynomial coefficients b0..b3 the oracle evaluates, so a digit dropped
+# in any coefficient of b0..b3 moves the recursion off every pole product.
+# The test finds the q whose pole product is closest to the oracle's
+# normalised recursion (a1, a2, a3): the published coefficients are rounded
+# to 5-6 digits, which leaves a best-fit residual below 3e-6 relative for
+# 0.5 <= sigma <= 8; a dropped digit in any of them leaves 1.3e-5 or more at
+# one of the sigmas below at least.
+M0, M1, M2 = 1.16680, 1.10783, 1.40586
+
+
+def _pole_product(q):
+    poles = [q / (M0 + q), q / (M1 + q + 1j * M2), q / (M1 + q - 1j * M2)]
+    return -np.real(np.poly(poles))[1:], poles   # a1, a2, a3 of w[t] = B x + sum a_i w[t-i]
+
+
+@pytest.mark.parametrize("sigma", [0.6, 1.0, 2.0, 3.0, 5.0, 8.0])
+def test_coefficients_are_the_published_pole_product(sigma):
+    from scipy.optimize import minimize_scalar
+    B, a1, a2, a3 = O.young_coefficients(sigma)
+    got = np.array([a1, a2, a3])
+
+    def resid(q):
+        expect, _ = _pole_product(q)
+        return float(np.max(np.abs(got - expect) / np.abs(expect)))
+
+    fit = minimize_scalar(resid, bounds=(0.05, 50.0), method="bounded", options={"xatol": 1e-12})
+    assert fit.fun <= 8e-6, fit.fun
+    # the gain is the product of (1 - p_i) of the same poles (unit DC gain), up to
+    # the coefficients' rounding carried through 1 - (a1 + a2 + a3)
+    _, poles = _pole_product(fit.x)
+    assert abs(B - float(np.real(np.prod([1 - p for p in poles])))) <= 1e-5 * (1 + np.abs(got).sum())
+
+
+@pytest.mark.parametrize("sigma", [1.0, 3.0, 8.0])
+def test_variance_of_the_impulse_response_has_the_closed_form(sigma):
+    # a causal filter B / prod(1 - p_i z^-1) has an impulse response of
+    # variance sum_i p_i / (1 - p_i)^2; the anticausal pass doubles it.
+    B, a1, a2, a3 = O.young_coefficients(sigma)
+    p = np.roots([1.0, -a1, -a2, -a3])
+    var_closed = 2.0 * float(np.real(np.sum(p / (1.0 - p) ** 2)))
+    L = 6000
+    x = np.zeros(L)
+    x[L // 2] = 1.0
+    y = O.young_1d(x, sigma)
+    t = np.arange(L) - L // 2
+    var_num = float((y * t * t).sum() / y.sum())
+    assert abs(var_num - var_closed) <= 1e-9 * var_closed
+    # the recursion's spread tracks sigma (Young and van Vliet's design gives a
+    # standard deviation a few to 25 per cent above sigma at these sizes)
+    assert sigma ** 2 <= var_closed <= 1.6 * sigma ** 2

@@ -1,9 +1,12 @@
 """hdf_apply_static: the fast-filter apply for callers that cannot allocate
-device memory (graph capture, frameworks that own all device memory, latency
--critical paths).  Its output must match the allocating path (hdf_create +
-hdf_set_centers + hdf_apply) on the same centres, call after call, although
-every call reuses the same static scratch array.  Kept in a file collected
-last so that a stop at its failure comes after every other test."""
+device memory (a framework that owns all device memory through its own pool,
+a latency-critical path where cudaMalloc/cudaFree would synchronise).  Its
+output must match the allocating path (hdf_create + hdf_set_centers +
+hdf_apply) on the same centres, call after call, although every call reuses
+the same static scratch array; it is also checked directly against the FP64
+oracle, and the device's free memory must not change across calls.  Kept in a
+file collected last so that a stop at its failure comes after every other
+test."""
 import ctypes as C
 
 import numpy as np
@@ -57,8 +60,32 @@ def test_static_apply_matches_allocating_apply_twice(mods, case):
         torch.cuda.synchronize()
         err = float((g - g_ref).abs().max())
         assert err <= TOL, (call, err)
+        ref_o = O.fast_filter(f_np.astype(np.float64), f_np.astype(np.float64),
+                              mu_np.astype(np.float64), ss, sr, O.window_halfwidth(ss))
+        err_o = float(np.max(np.abs(g.cpu().numpy() - ref_o)))
+        assert err_o <= TOL, (call, err_o)
         results.append(err)
+        ref.close()
     assert len(results) == 2
+
+
+def test_static_apply_allocates_nothing(mods):
+    """After a first call (which looks up the static array's address), further
+    calls leave the device's free memory unchanged."""
+    L, api = mods
+    f_np = synthetic.color_rectangles(96, 80, seed=63)
+    mu_np = O.bisecting_kmeans(f_np.reshape(3, -1).T.astype(np.float64), 8)[0].astype(np.float32)
+    f = torch.from_numpy(f_np).cuda()
+    mu = torch.from_numpy(mu_np).cuda()
+    g = torch.empty_like(f)
+    assert _static_apply(L, api, f, mu, 3.0, 0.2, g) == L.HDF_OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        assert _static_apply(L, api, f, mu, 3.0, 0.2, g) == L.HDF_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
 
 
 def test_static_apply_rejects_oversized_requests(mods):

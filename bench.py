@@ -1,12 +1,22 @@
 #!/usr/bin/env python
 """Benchmark of the fast high-dimensional bilateral filter on one or more GPUs.
 
-Workload: hyperspectral bilateral filtering, a 31 x 512 x 512 float32 cube of
-smooth spectral mixtures (guide = image), sigma_s = 5 (window 31 x 31),
-sigma_r = 0.3, K = 32 centres.  One step = the whole hot path of
-Algorithm 1 on the device: bisecting K-means of the guide, the FP64 fit of
-A^+, range maps b_k, coefficients c, the K(n+1) spatial convolutions and the
-combine/normalise.  Metric: megapixels per second (whole job).
+Headline workload: colour bilateral filtering of a 3 x 2048 x 2048 float32
+image of constant rectangles plus noise (guide = image), sigma_s = 8 (window
+49 x 49), sigma_r = 0.15, K = 16 centres -- the largest single-image
+configuration.  One step = the whole hot path of Algorithm 1 on the device:
+bisecting K-means of the guide, the FP64 fit of A^+, range maps b_k,
+coefficients c, the K(n+1) spatial convolutions, the combine/normalise with
+the denominator guard and the FP64 recomputation of ill-conditioned pixels.
+Metric: megapixels per second (whole job).
+
+Beside the headline the line carries, per named configuration (3x256^2 K=8;
+31x512^2 K=32; 1x1024^2 nonlocal means with a 6-feature PCA guide, K=32; the
+headline; the 64-image serving batch), the device time and MP/s, the GPU
+brute force (Eq. (1)-(2)) time and MP/s, PSNR of the fast filter against it,
+the same with bfloat16 guide storage, the guard and FP64-recomputation pixel
+counts, cond(A), and the max-abs difference from the FP64 oracle at sampled
+pixels (computed in the CPU-baseline leg).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -26,7 +36,7 @@ import subprocess
 import sys
 import time
 
-os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")   # the CPU oracle runs on one core
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")   # the CPU oracle runs one core per process
 os.environ.setdefault("OMP_NUM_THREADS", "1")
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -34,24 +44,25 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-WORKLOAD = dict(name="hyper512", bands=31, H=512, W=512, sigma_s=5.0, sigma_r=0.3, K=32)
+WORKLOAD = dict(name="color2048", n=3, H=2048, W=2048, sigma_s=8.0, sigma_r=0.15, K=16, S=24)
+EXTRA_CONFIGS = ["color256", "hyper512", "nlm1024"]
 METRIC = "megapixels/s of the fast filter (cluster + fit + filter) on one GB300"
 UNIT = "MP/s"
 L2_FLUSH_BYTES = 256 << 20          # larger than the 129 MB L2
-CPU_SAMPLE = 256                    # crop side of the oracle baseline sample
+CPU_CROP = 256                      # crop side of the oracle baseline sample
 REF_STEP_CROP = 128                 # crop side of one reference-arm step
+SAMPLED_PIXELS = 24                 # oracle pixels per configuration (plus the 4 corners)
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
 # ncu captures summarised under profiles/, valid only for the kernel source they
 # were taken on (sha256 prefix of the file that holds the kernel).
-NCU_TRAFFIC = {
-    "cluster_kernel": ("paper_1811_02363_gb300/csrc/cluster_kernel.cuh", "c017618119d5", 202.75e6),
-    "filter_tile_kernel": ("paper_1811_02363_gb300/csrc/filter_tile.cuh", "eacdca9e8b1b", 247.96e6),
-}
+NCU_TRAFFIC = {}
 
 
 def ncu_traffic(kernel: str):
     import hashlib
+    if kernel not in NCU_TRAFFIC:
+        return None
     path, sha, nbytes = NCU_TRAFFIC[kernel]
     try:
         cur = hashlib.sha256(open(os.path.join(ROOT, path), "rb").read()).hexdigest()[:12]
@@ -61,9 +72,9 @@ def ncu_traffic(kernel: str):
 
 
 def config(extra=None):
-    c = {"workload": "hyperspectral bilateral 31x512x512, sigma_s=5 (31x31 window), "
-                     "sigma_r=0.3, K=32, guide=image",
-         "pixels_per_step": WORKLOAD["H"] * WORKLOAD["W"], "channels": 31, "K": 32, "S": 15,
+    c = {"workload": "colour bilateral 3x2048x2048, sigma_s=8 (49x49 window), sigma_r=0.15, "
+                     "K=16, guide=image (12 constant rectangles + N(0, 0.05^2) noise)",
+         "pixels_per_step": WORKLOAD["H"] * WORKLOAD["W"], "channels": 3, "K": 16, "S": 24,
          "l2": "flushed between timed steps (256 MB write)"}
     if extra:
         c.update(extra)
@@ -93,18 +104,59 @@ def dist_env():
     return ws, rank, local
 
 
+def host_cpu() -> dict:
+    """Core count and CPU model of this host."""
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return {"nproc": cores, "model": model or platform.processor() or platform.machine(),
+            "machine": platform.machine()}
+
+
 # ---------------------------------------------------------------- CPU oracle
 
-def oracle_mps(crop: int) -> tuple[float, float]:
-    """Time the FP64 oracle (bisecting K-means + Algorithm 1) on a crop of the
-    workload; returns (MP/s, seconds)."""
-    from oracle import hdfilter_oracle as O
+def _headline_image():
     from paper_1811_02363_gb300 import synthetic
-    f = synthetic.hyperspectral_mixture(WORKLOAD["H"], WORKLOAD["W"], bands=31, seed=1)
-    f = f[:, :crop, :crop].astype(np.float64)
+    return synthetic.color_rectangles(WORKLOAD["H"], WORKLOAD["W"], seed=3)
+
+
+def _oracle_band(job):
+    """Algorithm 1 (FP64 oracle) on rows [y0, y1) of an image, computed on the
+    band widened by S rows on each side (the window's reach), so that the
+    rows returned equal those of the whole image."""
+    f, mu, sigma_s, sigma_r, S, y0, y1 = job
+    from oracle import hdfilter_oracle as O
+    a, b = max(0, y0 - S), min(f.shape[1], y1 + S)
+    g = O.fast_filter(f[:, a:b], f[:, a:b], mu, sigma_s, sigma_r, S)
+    return g[:, y0 - a:y1 - a]
+
+
+def oracle_crop(crop: int, cores: int = 1) -> tuple[float, float]:
+    """Time the FP64 oracle (bisecting K-means + Algorithm 1) on a crop of the
+    headline image; returns (MP/s, seconds).  With cores > 1 the filter runs
+    over row bands in that many processes (the clustering is sequential)."""
+    from oracle import hdfilter_oracle as O
+    f = _headline_image()[:, :crop, :crop].astype(np.float64)
+    n = f.shape[0]
     t0 = time.perf_counter()
-    mu, _, _ = O.bisecting_kmeans(f.reshape(31, -1).T, WORKLOAD["K"])
-    O.fast_filter(f, f, mu, WORKLOAD["sigma_s"], WORKLOAD["sigma_r"], 15)
+    mu, _, _ = O.bisecting_kmeans(f.reshape(n, -1).T, WORKLOAD["K"])
+    args = (WORKLOAD["sigma_s"], WORKLOAD["sigma_r"], WORKLOAD["S"])
+    if cores <= 1:
+        O.fast_filter(f, f, mu, *args)
+    else:
+        import multiprocessing as mp
+        edges = np.linspace(0, crop, cores + 1).astype(int)
+        jobs = [(f, mu, *args, int(edges[i]), int(edges[i + 1])) for i in range(cores)]
+        with mp.get_context("spawn").Pool(cores) as pool:
+            np.concatenate(pool.map(_oracle_band, jobs), axis=1)
     dt = time.perf_counter() - t0
     return crop * crop / dt / 1e6, dt
 
@@ -114,14 +166,15 @@ def run_reference(args) -> None:
     if rank != 0:
         return
     for _ in range(args.warmup):
-        oracle_mps(REF_STEP_CROP)
+        oracle_crop(REF_STEP_CROP)
     times = []
     for _ in range(args.steps):
-        _, dt = oracle_mps(REF_STEP_CROP)
+        _, dt = oracle_crop(REF_STEP_CROP)
         times.append(dt)
     total = sum(times)
     value = args.steps * REF_STEP_CROP ** 2 / total / 1e6
-    sample = f"{REF_STEP_CROP}x{REF_STEP_CROP} crop of the workload per step (all 31 bands, K=32)"
+    sample = (f"{REF_STEP_CROP}x{REF_STEP_CROP} crop of the workload per step (3 channels, "
+              f"K=16, S=24): bisecting K-means + Algorithm 1 in FP64")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
@@ -131,6 +184,19 @@ def run_reference(args) -> None:
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def oracle_sampled(item: dict) -> dict:
+    """Max-abs difference between the device's output and the FP64 oracle
+    (Eq. (13)-(16) from their definitions, the device's centres and guide) at
+    sampled pixels of one configuration; with the oracle's time."""
+    from oracle import hdfilter_oracle as O
+    t0 = time.perf_counter()
+    ref = O.fast_filter_at(item["f"], item["p"], item["mu"], item["sigma_s"], item["sigma_r"],
+                           item["S"], item["pix"])
+    err = float(np.max(np.abs(item["got"] - ref)))
+    return {"max_abs_vs_oracle": err, "oracle_pixels": int(len(item["pix"])),
+            "oracle_s": time.perf_counter() - t0}
 
 
 # ---------------------------------------------------------------- GPU
@@ -208,9 +274,137 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def run_gpu(args) -> None:
+def _timed(fn, reps: int, stream, flush) -> list[float]:
+    """ms of fn() over reps runs (CUDA events on `stream`), L2 flushed before each."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
+    for i in range(reps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        fn()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def _psnr(a, b) -> float:
+    """PSNR with peak 1 over all n|Omega| values (Eq. (21) reading)."""
+    import torch
+    mse = float(torch.mean((a.double() - b.double()) ** 2).item())
+    return float("inf") if mse == 0 else -10.0 * float(np.log10(mse))
+
+
+def _cond(flt):
+    """cond(A) = ratio of the extreme eigenvalues of the device's A^+ (full rank)."""
+    ev = np.linalg.eigvalsh(flt.get_pinv())
+    return float(ev.max() / ev.min()) if ev.min() > 0 else None
+
+
+def _sample_pixels(H: int, W: int, seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return np.concatenate([rng.integers(0, [H, W], size=(SAMPLED_PIXELS, 2)),
+                           np.array([[0, 0], [0, W - 1], [H - 1, 0], [H - 1, W - 1]])])
+
+
+def measure_config(name: str, reps: int, stream, flush, dev) -> tuple[dict, dict]:
+    """Device times, brute force, PSNR and the bfloat16-guide variant of one
+    named configuration; returns (figures, sampled outputs for the oracle)."""
     import torch
     from paper_1811_02363_gb300 import api, synthetic
+    w = synthetic.workload(name)
+    f_np = w["f"]
+    n, H, W = f_np.shape
+    f = torch.from_numpy(f_np).to(dev)
+    nlm = "patch" in w
+    rho = w["pca_dims"] if nlm else n
+    ss, sr, K = w["sigma_s"], w["sigma_r"], w["K"]
+    flt = api.HDFilter(H, W, n, rho, K, ss, sr)
+    out = {"image": f"{n}x{H}x{W}", "guide": f"{w['patch']}x{w['patch']} patches -> {rho} PCA "
+           "features (device)" if nlm else "image", "K": K, "S": flt.S, "sigma_s": ss,
+           "sigma_r": sr}
+    if nlm:
+        p = flt.nlm_guide(f, w["patch"])
+        out["guide_ms"] = statistics.median(
+            _timed(lambda: flt.nlm_guide(f, w["patch"], out=p), reps, stream, flush))
+    else:
+        p = f
+    g = torch.empty_like(f)
+
+    def step():
+        flt.cluster(p)
+        flt.apply(f, p, g)
+
+    for _ in range(3):
+        step()
+    ms = statistics.median(_timed(step, reps, stream, flush))
+    out["step_ms"] = ms
+    out["mps"] = H * W / (ms * 1e-3) / 1e6
+    out["cluster_fit_ms"] = statistics.median(_timed(lambda: flt.cluster(p), reps, stream, flush))
+    out["apply_ms"] = statistics.median(_timed(lambda: flt.apply(f, p, g), reps, stream, flush))
+    step()
+    st = flt.stats()
+    out.update(K_eff=st["K_eff"], fallback_pixels=st["fallback_pixels"],
+               rescued_pixels=st["rescued_pixels"], lloyd_iters_max=st["lloyd_iters_max"],
+               cond_A=_cond(flt))
+    gb = api.bruteforce(f, p, ss, sr)
+    bms = statistics.median(_timed(lambda: api.bruteforce(f, p, ss, sr, out=gb), 2, stream, flush))
+    out["bruteforce_ms"] = bms
+    out["bruteforce_mps"] = H * W / (bms * 1e-3) / 1e6
+    out["psnr_vs_bruteforce_db"] = _psnr(g, gb)
+    out["speedup_vs_bruteforce"] = bms / ms
+    if n > 3:   # band-averaged PSNR (MPSNR, the hyperspectral figure of Sec. IV)
+        bm = torch.mean((g.double() - gb.double()) ** 2, dim=(1, 2)).cpu().numpy()
+        out["mpsnr_vs_bruteforce_db"] = float(np.mean([-10.0 * np.log10(m) for m in bm if m > 0]))
+    # bfloat16 guide storage: clustering, range maps and coefficients read the
+    # rounded guide; the brute force keeps the float32 one
+    p16 = p.to(torch.bfloat16).contiguous()
+    f16 = api.HDFilter(H, W, n, rho, K, ss, sr, guide_dtype="bf16")
+    f16.cluster(p16)
+    g16 = f16.apply(f, p16)
+    ps16 = _psnr(g16, gb)
+    out["bf16_guide"] = {"psnr_vs_bruteforce_db": ps16,
+                         "psnr_loss_db": out["psnr_vs_bruteforce_db"] - ps16,
+                         "max_abs_vs_f32_guide": float((g16 - g).abs().max().item())}
+    f16.close()
+    pix = _sample_pixels(H, W, seed=H + n)
+    sample = {"f": f_np, "p": p.cpu().numpy().astype(np.float64) if nlm else f_np,
+              "mu": flt.get_centers().astype(np.float64), "sigma_s": ss, "sigma_r": sr,
+              "S": flt.S, "pix": pix, "got": g[:, pix[:, 0], pix[:, 1]].T.cpu().numpy()}
+    flt.close()
+    return out, sample
+
+
+def measure_batch(reps: int, stream, flush, dev) -> dict:
+    """The 64-image serving batch (sides 256..2048, RGB and 16-band, per-image
+    sigma_s, sigma_r, K; bfloat16 guides): one run = every stage of every
+    image, captured in a CUDA graph and replayed."""
+    import torch
+    from paper_1811_02363_gb300 import api, synthetic
+    items = synthetic.serving_batch(64, seed=4)
+    specs = [dict(H=it.image.shape[1], W=it.image.shape[2], n=it.image.shape[0], K=it.K,
+                  sigma_s=it.sigma_s, sigma_r=it.sigma_r, guide_dtype="bf16") for it in items]
+    fs = [torch.from_numpy(it.image).to(dev) for it in items]
+    gs = [torch.empty_like(x) for x in fs]
+    px = sum(s["H"] * s["W"] for s in specs)
+    b = api.Batch(specs)
+    b.bind(fs, gs)
+    for _ in range(2):
+        b.run(graph=True)
+    ms = statistics.median(_timed(lambda: b.run(graph=True), reps, stream, flush))
+    b.run(graph=False, timed=True)
+    t = b.times()
+    names = ["reset", "bf16_guides", "clustering", "fit", "range_maps", "tiles", "normalise"]
+    info = b.info()
+    b.close()
+    return {"images": len(specs), "megapixels": px / 1e6, "run_ms": ms,
+            "mps": px / (ms * 1e-3) / 1e6, "stage_ms": dict(zip(names, t)),
+            "launches_per_run": info["launches_per_run"], "graph_state": info["graph_state"]}
+
+
+def run_gpu(args) -> None:
+    import torch
+    from paper_1811_02363_gb300 import api
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -219,11 +413,12 @@ def run_gpu(args) -> None:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    H, W, K = WORKLOAD["H"], WORKLOAD["W"], WORKLOAD["K"]
-    f_host = synthetic.hyperspectral_mixture(H, W, bands=31, seed=1)
+    n, H, W, K = WORKLOAD["n"], WORKLOAD["H"], WORKLOAD["W"], WORKLOAD["K"]
+    ss, sr = WORKLOAD["sigma_s"], WORKLOAD["sigma_r"]
+    f_host = _headline_image()
     f = torch.from_numpy(f_host).to(dev)
     g = torch.empty_like(f)
-    flt = api.HDFilter(H, W, 31, 31, K, WORKLOAD["sigma_s"], WORKLOAD["sigma_r"])
+    flt = api.HDFilter(H, W, n, n, K, ss, sr)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -254,7 +449,6 @@ def run_gpu(args) -> None:
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    # dominant-kernel timing: the same steps split at the cluster/filter boundary
     mid = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     for i in range(args.steps):
         flush.zero_()
@@ -268,34 +462,35 @@ def run_gpu(args) -> None:
         dist.barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    cluster_ms = [a.elapsed_time(m) for (a, _), m in zip(ev, mid)]
-    apply_ms = [m.elapsed_time(b) for (_, b), m in zip(ev, mid)]
+    cluster_ms = statistics.median(a.elapsed_time(m) for (a, _), m in zip(ev, mid))
+    apply_ms = statistics.median(m.elapsed_time(b) for (_, b), m in zip(ev, mid))
     total_ms = slowest_rank_ms(sum(step_ms), dist, dev)
     value = job_mps(H * W, ws, args.steps, total_ms)
+    st = flt.stats()
 
-    # ---- filter-kernel timing (CUDA events around apply only, same stream)
-    ta = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    for i in range(args.steps):
+    # ---- the tile kernel's own duration: stage events inside hdf_apply
+    flt.set_stage_timing(True)
+    tile_ms, rm_ms, rest_ms = [], [], []
+    for _ in range(args.steps):
         flush.zero_()
-        ta[i][0].record(stream)
         flt.apply(f, f, g)
-        ta[i][1].record(stream)
-    torch.cuda.synchronize()
-    apply_only_ms = statistics.median(a.elapsed_time(b) for a, b in ta)
+        t = flt.stage_times()
+        rm_ms.append(t["rangemap"])
+        tile_ms.append(t["tile"])
+        rest_ms.append(t["rest"])
+    flt.set_stage_timing(False)
 
     # ---- end to end through the C ABI with host buffers: every step copies its
     # image from pinned host memory and reads its result back; the copies run on
-    # a copy stream, double-buffered, overlapping the neighbouring steps' compute
-    # (step i + 1's upload and step i's read-back run while the GPU filters).
+    # a copy stream, double-buffered, overlapping the neighbouring steps' compute.
     f_pin = torch.from_numpy(f_host).pin_memory()
     g_pin = torch.empty_like(f_pin).pin_memory()
     f_e = [torch.empty_like(f) for _ in range(2)]
     g_e = [torch.empty_like(f) for _ in range(2)]
     copy = torch.cuda.Stream(device=dev)
-    up = [torch.cuda.Event() for _ in range(2)]      # upload into f_e[b] done
-    done = [torch.cuda.Event() for _ in range(2)]    # step on buffer b computed
-    back = [torch.cuda.Event() for _ in range(2)]    # g_e[b] read back
+    up = [torch.cuda.Event() for _ in range(2)]
+    done = [torch.cuda.Event() for _ in range(2)]
+    back = [torch.cuda.Event() for _ in range(2)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     if dist:
@@ -313,11 +508,11 @@ def run_gpu(args) -> None:
         b = i & 1
         if i + 1 < args.steps:
             if i >= 1:
-                copy.wait_event(done[b ^ 1])   # step i - 1 no longer reads f_e[b ^ 1]
+                copy.wait_event(done[b ^ 1])
             upload(b ^ 1)
         stream.wait_event(up[b])
         if i >= 2:
-            stream.wait_event(back[b])         # step i - 2's result has left g_e[b]
+            stream.wait_event(back[b])
         flt.cluster(f_e[b])
         flt.apply(f_e[b], f_e[b], g_e[b])
         done[b].record(stream)
@@ -329,115 +524,92 @@ def run_gpu(args) -> None:
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_same = bool(torch.equal(g_pin, g.cpu()))   # the read-back equals the resident run
-    g = g_e[(args.steps - 1) & 1]
     e2e_ms = slowest_rank_ms(e0.elapsed_time(e1), dist, dev)
     e2e_value = job_mps(H * W, ws, args.steps, e2e_ms)
-    nbytes = f_host.nbytes
-
-    # ---- brute force on the same GPU (Eq. (1)-(2)) and the accuracy of the fast filter
-    gb = api.bruteforce(f, None, WORKLOAD["sigma_s"], WORKLOAD["sigma_r"])
-    torch.cuda.synchronize()
-    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    b0.record(stream)
-    api.bruteforce(f, None, WORKLOAD["sigma_s"], WORKLOAD["sigma_r"], out=gb)
-    b1.record(stream)
-    torch.cuda.synchronize()
-    brute_ms = b0.elapsed_time(b1)
-    flt.cluster(f)
-    flt.apply(f, f, g)
-    mse = float(torch.mean((g.double() - gb.double()) ** 2).item())
-    psnr = float("inf") if mse == 0 else -10.0 * np.log10(mse)
-    # band-averaged PSNR (MPSNR, the hyperspectral quality figure of Sec. IV)
-    band_mse = torch.mean((g.double() - gb.double()) ** 2, dim=(1, 2)).cpu().numpy()
-    mpsnr = float(np.mean([float("inf") if m == 0 else -10.0 * np.log10(m) for m in band_mse]))
-    st = flt.stats()
-
-    # ---- the box spatial kernel (omega = 1 on W, Sec. III's NLM kernel) on the
-    # same image and centres: apply-only time and PSNR against its brute force
-    fb = api.HDFilter(H, W, 31, 31, K, WORKLOAD["sigma_s"], WORKLOAD["sigma_r"], S=15, spatial="box")
-    fb.set_centers(flt.get_centers())
-    gbx = torch.empty_like(f)
-    fb.apply(f, f, gbx)
-    tb = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    for i in range(args.steps):
-        flush.zero_()
-        tb[i][0].record(stream)
-        fb.apply(f, f, gbx)
-        tb[i][1].record(stream)
-    torch.cuda.synchronize()
-    box_ms = statistics.median(a.elapsed_time(b) for a, b in tb)
-    gbb = api.bruteforce(f, None, WORKLOAD["sigma_s"], WORKLOAD["sigma_r"], S=15, spatial="box")
-    torch.cuda.synchronize()
-    bmse = float(torch.mean((gbx.double() - gbb.double()) ** 2).item())
-    box = {"spatial": "box, S=15 (31x31 window), same centres", "apply_ms": box_ms,
-           "apply_mps": H * W / (box_ms * 1e-3) / 1e6,
-           "psnr_vs_box_bruteforce_db": float("inf") if bmse == 0 else -10.0 * np.log10(bmse)}
-    fb.close()
+    flt.close()
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
 
-    # ---- roofline of the dominant kernel and of the filter kernel
+    # ---- every configuration, the serving batch, the measured peaks
+    fp32_peak, fp64_peak = api.probe_peaks()
+    reps = max(5, min(args.steps, 10))
+    configs, samples = {}, {}
+    for name in EXTRA_CONFIGS + [WORKLOAD["name"]]:
+        configs[name], samples[name] = measure_config(name, reps, stream, flush, dev)
+    configs["serving64"] = measure_batch(3, stream, flush, dev)
+    hl = configs[WORKLOAD["name"]]
+
+    # ---- roofline of the tile kernel (FP32 FIR arithmetic) and the clustering
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak_tflops = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    K_eff, S = st["K_eff"], WORKLOAD["S"]
     npx = H * W
-    # Clustering: a model of plain Lloyd traffic, rho*4 B per point
-    # per assignment pass, 20 passes per level, log2 K levels.
-    cl_bytes = npx * 31 * 4 * 20 * 5
-    cl_s = statistics.median(cluster_ms) * 1e-3
-    # Filter: 4 (2S+1) K (n+1) FLOP per pixel for the two 1-D passes (FMA = 2).
-    fir_flops = npx * 4 * (2 * 15 + 1) * K * 32
-    ap_s = apply_only_ms * 1e-3
-    rf_cluster = {"kernel": "cluster_kernel", "bound": "hbm", "achieved": cl_bytes / cl_s / 1e9,
-                  "peak": hbm, "unit": "GB/s", "frac": cl_bytes / cl_s / 1e9 / hbm,
-                  "traffic": ncu_traffic("cluster_kernel"), "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
-                  "algorithmic_bytes_per_launch": cl_bytes}
-    rf_filter = {"kernel": "filter_tile_kernel (+ range maps, divide)", "bound": "alu",
-                 "achieved": fir_flops / ap_s / 1e12, "peak": fp32_peak_tflops,
-                 "unit": "TFLOP/s", "frac": fir_flops / ap_s / 1e12 / fp32_peak_tflops,
-                 "traffic": ncu_traffic("filter_tile_kernel"),
-                 "peak_source": "152 SM x 128 FP32 lanes x 2 x max SM clock (derived)",
-                 "algorithmic_flops_per_launch": fir_flops}
-    dominant = rf_cluster if statistics.median(cluster_ms) >= apply_only_ms else rf_filter
+    fir_flops = npx * 4 * (2 * S + 1) * K_eff * (n + 1)   # two 1-D passes, FMA = 2 FLOP
+    tile_s = statistics.median(tile_ms) * 1e-3
+    rf_tile = {"kernel": "filter_tile_kernel<24,2,64,Gaussian> (row + column FIR, combine)",
+               "bound": "alu", "achieved": fir_flops / tile_s / 1e12, "peak": fp32_peak,
+               "unit": "TFLOP/s", "frac": fir_flops / tile_s / 1e12 / fp32_peak,
+               "traffic": ncu_traffic("filter_tile_kernel"),
+               "peak_source": "measured FP32 FMA rate (hdf_probe_peaks, this run)",
+               "algorithmic_flops_per_launch": fir_flops, "launch_ms": tile_s * 1e3}
+    cl_bytes = npx * (4 * n + 4)          # one read of the guide, one write of the labels
+    cl_s = cluster_ms * 1e-3
+    rf_cluster = {"kernel": "cluster_kernel<4> (bisecting K-means, one cooperative launch) + fit",
+                  "bound": "hbm", "achieved": cl_bytes / cl_s / 1e9, "peak": hbm,
+                  "unit": "GB/s", "frac": cl_bytes / cl_s / 1e9 / hbm,
+                  "traffic": ncu_traffic("cluster_kernel"),
+                  "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+                  "algorithmic_bytes_per_launch": cl_bytes, "launch_ms": cluster_ms,
+                  "note": "latency bound: the points stay in L2 between its ~100 grid-wide "
+                          "steps; algorithmic bytes = one guide read + the labels"}
+    dominant = rf_cluster if cluster_ms > statistics.median(tile_ms) else rf_tile
 
-    cpu = None
-    if ws == 1 or rank == 0:
-        cpu_v, cpu_s = oracle_mps(CPU_SAMPLE)
-        cpu = {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{CPU_SAMPLE}x{CPU_SAMPLE} crop of the workload, clustering + "
-                         f"Algorithm 1 in FP64 ({cpu_s:.1f} s)"}
+    # ---- CPU legs: the oracle timed on this host's cores, and the oracle at
+    # sampled pixels of every configuration against the device's outputs
+    cpu_host = host_cpu()
+    cpu1_v, cpu1_s = oracle_crop(CPU_CROP, 1)
+    cores = max(1, int(cpu_host["nproc"] or 1))
+    cpuN_v, cpuN_s = oracle_crop(CPU_CROP, cores) if cores > 1 else (cpu1_v, cpu1_s)
+    for name, smp in samples.items():
+        configs[name].update(oracle_sampled(smp))
+    sample = (f"{CPU_CROP}x{CPU_CROP} crop of the workload: bisecting K-means + Algorithm 1 "
+              f"in FP64 ({cpu1_s:.1f} s on 1 core)")
+    cpu = {"value": cpu1_v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+           "all_cores": {"value": cpuN_v, "cores": cores, "seconds": cpuN_s,
+                         "how": "clustering on one core, Algorithm 1 over row bands in "
+                                "spawned processes"},
+           "host": cpu_host}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": config({"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"}),
             "roofline": dominant,
-            "roofline_kernels": [rf_cluster, rf_filter],
+            "roofline_kernels": [rf_tile, rf_cluster],
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes,
-                    "d2h_bytes_per_step": nbytes,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": f_host.nbytes,
+                    "d2h_bytes_per_step": f_host.nbytes,
                     "copies": "pinned, on a copy stream, double-buffered, overlapping the "
                               "neighbouring steps' compute",
                     "result_equals_resident_run": e2e_same},
-            "gpu_launches": 6 * args.steps,
+            "gpu_launches": 7 * args.steps,
             "clocks": clk,
-            "breakdown_ms": {"cluster_fit": statistics.median(cluster_ms),
-                             "apply": statistics.median(apply_ms),
-                             "apply_only": apply_only_ms},
-            "bruteforce_gpu": {"value": npx / (brute_ms * 1e-3) / 1e6, "unit": UNIT,
-                               "ms": brute_ms},
-            "psnr_vs_bruteforce_db": psnr,
-            "mpsnr_vs_bruteforce_db": mpsnr,
-            "box_kernel": box,
+            "breakdown_ms": {"cluster_fit": cluster_ms, "apply": apply_ms,
+                             "apply_rangemap": statistics.median(rm_ms),
+                             "apply_tile": statistics.median(tile_ms),
+                             "apply_divide_fixup_rescue": statistics.median(rest_ms)},
+            "bruteforce_gpu": {"value": hl["bruteforce_mps"], "unit": UNIT,
+                               "ms": hl["bruteforce_ms"]},
+            "psnr_vs_bruteforce_db": hl["psnr_vs_bruteforce_db"],
+            "measured_peaks_tflops": {"fp32": fp32_peak, "fp64": fp64_peak},
+            "configs": configs,
             "stats": st}
     print(json.dumps(line), flush=True)
     if dist:

@@ -98,6 +98,10 @@ typedef struct {
   int lloyd_iters_max;   /* largest 2-means iteration count of the last clustering */
   int rounds;            /* parallel split rounds of the last clustering */
   double cluster_error;  /* E_K = sum_k sum_{i in C_k} |p(i) - mu_k|^2 (Theorem 1) */
+  int rescued_pixels;    /* pixels of the last hdf_apply recomputed in FP64: their float32
+                            denominator sum_k c_k r_k was ill-conditioned (sum_k |c_k| r_k
+                            above 64 times its magnitude) or within rounding of the guard's
+                            threshold; counted in fallback_pixels when the FP64 guard fires */
 } hdf_stats;
 
 /* Validate `desc`, fill in S if 0, and allocate the device workspace of one
@@ -111,6 +115,28 @@ hdf_status hdf_create(hdf_handle** out, const hdf_desc* desc);
 
 /* Release everything hdf_create allocated.  Synchronises the device. */
 void hdf_destroy(hdf_handle* h);
+
+/* Limit of each device-side wait of hdf_cluster (its grid barriers, the wait
+ * of a split's finishing block for the other blocks' partial sums, and the
+ * completion of its bulk copies), in seconds, 0..60; the default is 2 s.  A
+ * wait that reaches the limit records HDF_ETIMEOUT in the device status word
+ * and every block of the launch returns (after its own copies in flight have
+ * landed); hdf_get_stats then reports HDF_ETIMEOUT and the centres are not
+ * valid.  For failure handling and its tests; not part of the paper's method.
+ * Errors: HDF_EINVAL (NULL handle, limit outside 0..60). */
+hdf_status hdf_set_wait_limit(hdf_handle* h, double seconds);
+
+/* Stage timing of hdf_apply, for measurement: with on != 0 every following
+ * hdf_apply records CUDA events on its stream before the range maps, after
+ * them, after the convolution tile kernel and after the last stage
+ * (normalisation, guard fix-up, FP64 recomputation).  hdf_get_stage_times
+ * then returns the three intervals of the last apply in ms: range maps, tile
+ * kernel, the rest (the tile kernel's interval is 0 for the recursive
+ * Gaussian).  Creates the events on first use (no device memory); the
+ * getter synchronises with the last event.  Not part of the paper's method.
+ * Errors: HDF_EINVAL (NULL, or no timed apply yet). */
+hdf_status hdf_set_stage_timing(hdf_handle* h, int on);
+hdf_status hdf_get_stage_times(hdf_handle* h, float* h_ms, int cap, int* count);
 
 /* The descriptor in effect (S filled in). */
 hdf_status hdf_get_desc(const hdf_handle* h, hdf_desc* out);
@@ -145,7 +171,10 @@ hdf_status hdf_get_labels(hdf_handle* h, int32_t* d_labels, void* stream);
  * with the centres installed by hdf_cluster or hdf_set_centers.
  * d_f: (n, H, W) float32; d_p: guide (rho, H, W); d_g: output (n, H, W)
  * float32, must not alias d_f or d_p.  Where sum_k c_k r_k <= 1e-6 max_k r_k
- * the pixel takes the indicator value v_s / r_s (s = nearest centre).
+ * the pixel takes the indicator value v_s / r_s (s = nearest centre).  Pixels
+ * whose float32 sums are ill-conditioned (see hdf_stats.rescued_pixels) are
+ * recomputed in FP64 from Eq. (13)-(16) and their guard decided in FP64
+ * (Gaussian and box kernels; the recursive Gaussian keeps float32).
  * Asynchronous, allocates nothing. */
 hdf_status hdf_apply(hdf_handle* h, const float* d_f, const void* d_p, float* d_g,
                      void* stream);
@@ -177,7 +206,7 @@ hdf_status hdf_backward(hdf_handle* h, const float* d_f, const void* d_p,
  *         HDF_EUNSUPPORTED before anything is enqueued).
  *   d_mu: device float32 centres, K x rho row-major (caller-owned, read only).
  *   d_f, d_p, d_g: as in hdf_apply.
- * A call needs about K*K*12 + H*W*(8*K + 13) bytes of that array; larger
+ * A call needs about K*K*12 + H*W*(8*K + 17) bytes of that array; larger
  * requests return HDF_EUNSUPPORTED without enqueuing anything (e.g. K = 32 at
  * 256 x 256 fits, K = 32 at 512 x 512 does not).  No cudaMalloc, cudaFree or
  * allocating library call is made.  The first call on a device looks up the
@@ -202,6 +231,22 @@ hdf_status hdf_apply_static(const hdf_desc* desc, const float* d_mu, int K, cons
  * odd patch, desc.n * patch^2 <= 96, desc.n <= 4, H, W > patch/2; otherwise
  * HDF_EUNSUPPORTED / HDF_EINVAL.  Asynchronous, allocates nothing. */
 hdf_status hdf_nlm_guide(hdf_handle* h, const float* d_f, int patch, float* d_p, void* stream);
+
+/* Guide for an anisotropic range kernel (Sec. III-E: separate widths for the
+ * low-light and the infrared dimensions of a nonlocal-means guide):
+ * d_out[d] = d_p[d] / sigma_r[d] for each of the rho planes.  The
+ * anisotropic Gaussian phi(x) = exp(-sum_d x_d^2 / (2 sigma_r[d]^2)) of p is
+ * the isotropic Gaussian of unit width of this scaled guide, so hdf_create /
+ * hdf_cluster / hdf_apply / hdf_bruteforce / the batch with sigma_r = 1 and
+ * the scaled guide filter with the anisotropic kernel (the clustering then
+ * runs in the kernel's metric; centres come out in scaled units).
+ *   d_p: guide (rho, H, W) float32 or bfloat16 (guide_dtype);
+ *   h_sigma_r: host, rho widths > 0;  d_out: (rho, H, W) float32, may equal
+ *   d_p for a float32 guide.
+ * Asynchronous, allocates nothing.  Errors: HDF_EINVAL (NULL, width <= 0 or
+ * not finite, bad dtype), HDF_EUNSUPPORTED (rho > HDF_MAX_RHO). */
+hdf_status hdf_scale_guide(const void* d_p, int guide_dtype, int rho, int H, int W,
+                           const double* h_sigma_r, float* d_out, void* stream);
 
 /* Brute-force filter, Eq. (1)-(2), by direct summation over the window.
  * Same layouts as hdf_apply.  Asynchronous, allocates nothing. */
@@ -332,6 +377,14 @@ hdf_status hdf_batch_get_stats(hdf_batch* b, int i, hdf_stats* out);
 
 /* Plan and state of the batch. */
 hdf_status hdf_batch_get_info(hdf_batch* b, hdf_batch_info* out);
+
+/* Measured peak rates of this device's FP32 and FP64 FMA pipes (FLOP/s,
+ * FMA = 2 FLOP), in TFLOP/s: FMA-chain probe kernels over every SM, timed
+ * with CUDA events on `stream` (best of three launches after a warm-up).
+ * The denominators of the FP32-bound kernels' roofline fractions.
+ * Synchronises `stream`.  Measurement support; not part of the paper's
+ * method.  Errors: HDF_EINVAL (NULL output), HDF_ECUDA. */
+hdf_status hdf_probe_peaks(double* fp32_tflops, double* fp64_tflops, void* stream);
 
 /* Human-readable name of a status code. */
 const char* hdf_status_string(hdf_status s);

@@ -71,6 +71,40 @@ def range_kernel(sq_dist: np.ndarray, sigma_r: float) -> np.ndarray:
     return np.exp(-sq_dist / (2.0 * sigma_r * sigma_r))
 
 
+def is_anisotropic(sigma_r) -> bool:
+    """sigma_r given per guide dimension (a sequence) rather than as one number."""
+    return np.ndim(sigma_r) > 0
+
+
+def range_kernel_diff(diff: np.ndarray, sigma_r, axis: int) -> np.ndarray:
+    """phi of the differences `diff`, the guide dimension along `axis`.
+    With one sigma_r: the isotropic Gaussian of Sec. III.  With one sigma_r
+    per dimension: the anisotropic Gaussian of Sec. III-E (a separate width
+    for the low-light and the infrared dimensions of the guide),
+      phi(x) = exp(-sum_d x_d^2 / (2 sigma_{r,d}^2))."""
+    diff = np.asarray(diff, dtype=np.float64)
+    if not is_anisotropic(sigma_r):
+        return range_kernel((diff ** 2).sum(axis=axis), sigma_r)
+    s = np.asarray(sigma_r, dtype=np.float64)
+    ax = axis % diff.ndim
+    if s.shape != (diff.shape[ax],):
+        raise ValueError("one sigma_r per guide dimension")
+    shape = [1] * diff.ndim
+    shape[ax] = -1
+    return np.exp(-((diff ** 2) / (2.0 * s * s).reshape(shape)).sum(axis=axis))
+
+
+def scaled_guide(p: np.ndarray, sigma_r) -> np.ndarray:
+    """The guide in the units of the anisotropic kernel's exponent: dimension d
+    divided by sigma_{r,d}, so that the anisotropic Gaussian of p is the
+    isotropic one of unit width of the scaled guide.  Reading (the paper is
+    silent): with an anisotropic kernel the clustering of Theta, Sec. II-C,
+    runs in these units, the metric the kernel uses (Theorem 1's Lipschitz
+    bound holds in it); so does the nearest-centre choice of Eq. (17)."""
+    s = np.asarray(sigma_r, dtype=np.float64)
+    return np.asarray(p, dtype=np.float64) / s.reshape(-1, *([1] * (np.ndim(p) - 1)))
+
+
 # --------------------------------------------------------------------------
 # Brute force: Eq. (1) and Eq. (2)
 # --------------------------------------------------------------------------
@@ -99,7 +133,7 @@ def bruteforce(f: np.ndarray, p: np.ndarray, sigma_s: float, sigma_r: float,
                 continue
             pi = p[:, y0:y1, x0:x1]
             pn = p[:, y0 - j1:y1 - j1, x0 - j2:x1 - j2]
-            wt = w * range_kernel(((pn - pi) ** 2).sum(axis=0), sigma_r)
+            wt = w * range_kernel_diff(pn - pi, sigma_r, axis=0)
             num[:, y0:y1, x0:x1] += wt * f[:, y0 - j1:y1 - j1, x0 - j2:x1 - j2]
             den[y0:y1, x0:x1] += wt
     return num / den
@@ -119,8 +153,7 @@ def bruteforce_at(f: np.ndarray, p: np.ndarray, sigma_s: float, sigma_r: float,
         dy = (y - np.arange(ya, yb, dtype=np.float64))[:, None]
         dx = (x - np.arange(xa, xb, dtype=np.float64))[None, :]
         w = spatial_weight(dy, dx, sigma_s, spatial)
-        d2 = ((p[:, ya:yb, xa:xb] - p[:, y:y + 1, x:x + 1]) ** 2).sum(axis=0)
-        wt = w * range_kernel(d2, sigma_r)
+        wt = w * range_kernel_diff(p[:, ya:yb, xa:xb] - p[:, y:y + 1, x:x + 1], sigma_r, axis=0)
         out[m] = (wt * f[:, ya:yb, xa:xb]).sum(axis=(1, 2)) / wt.sum()
     return out
 
@@ -209,11 +242,16 @@ def clustering_error(P: np.ndarray, mu: np.ndarray, labels: np.ndarray) -> float
     return float(((P - mu[labels]) ** 2).sum())
 
 
-def nearest_center(p: np.ndarray, mu: np.ndarray) -> np.ndarray:
+def nearest_center(p: np.ndarray, mu: np.ndarray, sigma_r=None) -> np.ndarray:
     """s(i) = argmin_k |p(i) - mu_k|^2, ties -> lowest k (the membership
-    "p(i) in C_s" of Eq. (17), read as the Voronoi cell of mu_s).  Returns
-    (H, W) int."""
+    "p(i) in C_s" of Eq. (17), read as the Voronoi cell of mu_s); with an
+    anisotropic kernel the distance is taken in its units (scaled_guide).
+    Returns (H, W) int."""
     p = np.asarray(p, dtype=np.float64)
+    mu = np.asarray(mu, dtype=np.float64)
+    if is_anisotropic(sigma_r):
+        p = scaled_guide(p, sigma_r)
+        mu = mu / np.asarray(sigma_r, dtype=np.float64)[None, :]
     d2 = ((p[None, :, :, :] - mu[:, :, None, None]) ** 2).sum(axis=1)
     return np.argmin(d2, axis=0)
 
@@ -225,6 +263,8 @@ def nearest_center(p: np.ndarray, mu: np.ndarray) -> np.ndarray:
 def kernel_matrix(mu: np.ndarray, sigma_r: float) -> np.ndarray:
     """A_kl = phi(mu_k - mu_l) (Eq. (12))."""
     mu = np.asarray(mu, dtype=np.float64)
+    if is_anisotropic(sigma_r):
+        return range_kernel_diff(mu[:, None, :] - mu[None, :, :], sigma_r, axis=2)
     d2 = ((mu[:, None, :] - mu[None, :, :]) ** 2).sum(axis=2)
     return range_kernel(d2, sigma_r)
 
@@ -250,6 +290,8 @@ def range_maps(p: np.ndarray, mu: np.ndarray, sigma_r: float) -> np.ndarray:
     """b_k(i) = phi(mu_k - p(i)) (Eq. (12)).  Returns (K, H, W)."""
     p = np.asarray(p, dtype=np.float64)
     mu = np.asarray(mu, dtype=np.float64)
+    if is_anisotropic(sigma_r):
+        return range_kernel_diff(p[None, :, :, :] - mu[:, :, None, None], sigma_r, axis=1)
     d2 = ((p[None, :, :, :] - mu[:, :, None, None]) ** 2).sum(axis=1)
     return range_kernel(d2, sigma_r)
 
@@ -383,7 +425,7 @@ def fast_filter(f: np.ndarray, p: np.ndarray, mu: np.ndarray, sigma_s: float,
     A = kernel_matrix(mu, sigma_r)
     A_pinv = pinv_psd(A)
     B = range_maps(p, mu, sigma_r)                                   # (K, H, W)
-    s = nearest_center(p, mu)
+    s = nearest_center(p, mu, sigma_r)
     if variant == "opt":
         C = np.einsum("kl,lhw->khw", A_pinv, B)
     elif variant == "indicator":
@@ -394,6 +436,7 @@ def fast_filter(f: np.ndarray, p: np.ndarray, mu: np.ndarray, sigma_s: float,
         raise ValueError(variant)
     v = np.zeros((n, H, W))
     r = np.zeros((H, W))
+    r_abs = np.zeros((H, W))          # sum_k |c_k| r_k: the scale of the denominator's rounding
     r_max = np.zeros((H, W))
     v_s = np.zeros((n, H, W))
     r_s = np.zeros((H, W))
@@ -402,6 +445,7 @@ def fast_filter(f: np.ndarray, p: np.ndarray, mu: np.ndarray, sigma_s: float,
         rk = spatial_conv(B[k], sigma_s, S, spatial)                # omega * b_k
         v += C[k] * vk
         r += C[k] * rk
+        r_abs += np.abs(C[k]) * rk
         np.maximum(r_max, rk, out=r_max)
         sel = s == k
         v_s[:, sel] = vk[:, sel]
@@ -413,7 +457,8 @@ def fast_filter(f: np.ndarray, p: np.ndarray, mu: np.ndarray, sigma_s: float,
         ind = np.where(r_s > 0, v_s / np.where(r_s > 0, r_s, 1.0), f)
         g = np.where(fallback[None], ind, g)
     if return_stats:
-        return g, dict(fallback=int(fallback.sum()), A=A, A_pinv=A_pinv)
+        return g, dict(fallback=int(fallback.sum()), A=A, A_pinv=A_pinv,
+                       fallback_mask=fallback, den=r, den_abs=r_abs, r_max=r_max)
     return g
 
 
@@ -429,6 +474,8 @@ def ls_coefficients(p: np.ndarray, mu: np.ndarray, sigma_r: float, S: int) -> np
     calls this impractically slow and keeps it only to compare with Eq. (11)
     (its Fig. 6); it is here for that comparison on small images.
     Returns C (K, H, W)."""
+    if is_anisotropic(sigma_r):
+        raise ValueError("the least-squares coefficients are written for the isotropic kernel")
     p = np.asarray(p, dtype=np.float64)
     mu = np.asarray(mu, dtype=np.float64)
     rho, H, W = p.shape
@@ -464,12 +511,13 @@ def fast_filter_at(f: np.ndarray, p: np.ndarray, mu: np.ndarray, sigma_s: float,
         dx = (x - np.arange(xa, xb, dtype=np.float64))[None, :]
         w = spatial_weight(dy, dx, sigma_s, spatial)
         pw = p[:, ya:yb, xa:xb]
-        d2w = ((pw[None] - mu[:, :, None, None]) ** 2).sum(axis=1)   # (K, h, w)
-        phi = range_kernel(d2w, sigma_r)
+        phi = range_kernel_diff(pw[None] - mu[:, :, None, None], sigma_r, axis=1)   # (K, h, w)
         vk = np.einsum("hw,khw,nhw->kn", w, phi, f[:, ya:yb, xa:xb])  # Eq. (13)
         rk = np.einsum("hw,khw->k", w, phi)                          # Eq. (14)
-        d2i = ((p[:, y, x][None, :] - mu) ** 2).sum(axis=1)
-        b = range_kernel(d2i, sigma_r)
+        b = range_kernel_diff(p[:, y, x][None, :] - mu, sigma_r, axis=1)
+        d2i = ((scaled_guide(p[:, y, x], sigma_r)[None, :] - mu / np.asarray(sigma_r))
+               ** 2).sum(axis=1) if is_anisotropic(sigma_r) else \
+            ((p[:, y, x][None, :] - mu) ** 2).sum(axis=1)
         c = A_pinv @ b
         num = c @ vk
         den = float(c @ rk)

@@ -26,7 +26,7 @@ class hdf_desc(C.Structure):
 class hdf_stats(C.Structure):
     _fields_ = [("K_eff", C.c_int), ("fallback_pixels", C.c_int), ("device_error", C.c_int),
                 ("lloyd_iters_max", C.c_int), ("rounds", C.c_int),
-                ("cluster_error", C.c_double)]
+                ("cluster_error", C.c_double), ("rescued_pixels", C.c_int)]
 
 
 HDF_BATCH_GRAPH, HDF_BATCH_TIMED, HDF_BATCH_SKIP_CLUSTER = 1, 2, 4
@@ -48,6 +48,9 @@ _P = C.c_void_p
 SIGNATURES = [
     ("hdf_create", C.c_int, [C.POINTER(_P), C.POINTER(hdf_desc)]),
     ("hdf_destroy", None, [_P]),
+    ("hdf_set_wait_limit", C.c_int, [_P, C.c_double]),
+    ("hdf_set_stage_timing", C.c_int, [_P, C.c_int]),
+    ("hdf_get_stage_times", C.c_int, [_P, _P, C.c_int, C.POINTER(C.c_int)]),
     ("hdf_get_desc", C.c_int, [_P, C.POINTER(hdf_desc)]),
     ("hdf_cluster", C.c_int, [_P, _P, _P]),
     ("hdf_set_centers", C.c_int, [_P, _P, C.c_int, _P]),
@@ -58,6 +61,7 @@ SIGNATURES = [
     ("hdf_backward", C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     ("hdf_nlm_guide", C.c_int, [_P, _P, C.c_int, _P, _P]),
     ("hdf_apply_static", C.c_int, [C.POINTER(hdf_desc), _P, C.c_int, _P, _P, _P, _P]),
+    ("hdf_scale_guide", C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P, _P]),
     ("hdf_bruteforce", C.c_int, [C.POINTER(hdf_desc), _P, _P, _P, _P]),
     ("hdf_get_trace", C.c_int, [_P, _P, C.c_int, C.POINTER(C.c_int), _P]),
     ("hdf_get_stats", C.c_int, [_P, C.POINTER(hdf_stats), _P]),
@@ -73,6 +77,7 @@ SIGNATURES = [
     ("hdf_batch_get_centers", C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_int)]),
     ("hdf_batch_get_stats", C.c_int, [_P, C.c_int, C.POINTER(hdf_stats)]),
     ("hdf_batch_get_info", C.c_int, [_P, C.POINTER(hdf_batch_info)]),
+    ("hdf_probe_peaks", C.c_int, [_P, _P, _P]),
     ("hdf_status_string", C.c_char_p, [C.c_int]),
     ("hdf_last_cuda_error", C.c_char_p, []),
 ]

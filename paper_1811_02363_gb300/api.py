@@ -172,6 +172,22 @@ class HDFilter:
                                       _stream()), "hdf_get_trace")
         return buf[:2 * n.value].reshape(-1, 2)
 
+    def set_stage_timing(self, on: bool = True) -> None:
+        """Record CUDA events between the stages of every following apply."""
+        L.check(L.lib().hdf_set_stage_timing(self._h, 1 if on else 0), "hdf_set_stage_timing")
+
+    def stage_times(self) -> dict:
+        """ms of the last timed apply: range maps, tile kernel, the rest."""
+        arr = (C.c_float * 3)()
+        cnt = C.c_int()
+        L.check(L.lib().hdf_get_stage_times(self._h, arr, 3, C.byref(cnt)), "hdf_get_stage_times")
+        names = ["rangemap", "tile", "rest"]
+        return {names[i]: float(arr[i]) for i in range(cnt.value)}
+
+    def set_wait_limit(self, seconds: float) -> None:
+        """Limit of each device-side wait of ``cluster`` (default 2 s)."""
+        L.check(L.lib().hdf_set_wait_limit(self._h, float(seconds)), "hdf_set_wait_limit")
+
     def stats(self) -> dict:
         s = L.hdf_stats()
         code = L.lib().hdf_get_stats(self._h, C.byref(s), _stream())
@@ -179,6 +195,31 @@ class HDFilter:
         if code != L.HDF_OK:
             raise L.HDFError(code, "device status")
         return d
+
+
+def scale_guide(p: torch.Tensor, sigma_r, out: torch.Tensor | None = None) -> torch.Tensor:
+    """The guide divided by sigma_r per dimension (hdf_scale_guide): with it
+    and sigma_r = 1 every filter call uses the anisotropic range kernel
+    exp(-sum_d x_d^2 / (2 sigma_r[d]^2)) of Sec. III-E."""
+    if not p.is_cuda or p.dim() != 3 or not p.is_contiguous():
+        raise ValueError("p must be a contiguous CUDA (rho, H, W) tensor")
+    if p.dtype not in (torch.float32, torch.bfloat16):
+        raise ValueError("p must be float32 or bfloat16")
+    rho, H, W = p.shape
+    sr = np.ascontiguousarray(np.broadcast_to(np.asarray(sigma_r, dtype=np.float64), (rho,)))
+    q = torch.empty((rho, H, W), dtype=torch.float32, device=p.device) if out is None else out
+    _check_image(q, "out")
+    gd = L.HDF_GUIDE_F32 if p.dtype == torch.float32 else L.HDF_GUIDE_BF16
+    L.check(L.lib().hdf_scale_guide(_ptr(p), gd, rho, H, W, sr.ctypes.data_as(C.c_void_p), _ptr(q),
+                                    _stream()), "hdf_scale_guide")
+    return q
+
+
+def probe_peaks() -> tuple[float, float]:
+    """Measured FP32 and FP64 FMA peak rates of the current GPU, TFLOP/s."""
+    a, b = C.c_double(), C.c_double()
+    L.check(L.lib().hdf_probe_peaks(C.byref(a), C.byref(b), _stream()), "hdf_probe_peaks")
+    return a.value, b.value
 
 
 def bruteforce(f: torch.Tensor, p: torch.Tensor | None, sigma_s: float, sigma_r: float,

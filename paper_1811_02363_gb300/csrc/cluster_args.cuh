@@ -7,16 +7,13 @@
 namespace hdf {
 namespace clus {
 
-constexpr int CL_THREADS = 256;
-constexpr int CL_WARPS = CL_THREADS / 32;
-constexpr int PPT = 8;                  // points per thread per chunk
-constexpr int CH = CL_THREADS * PPT;    // points per chunk
+constexpr int CH = 2048;                // points per chunk (the workspace layout depends on it)
 constexpr int MAXACT = 32;              // splits per round
 constexpr int MAXSEG = 2 * MAXACT;
 constexpr int MAXNODES = 16 * HDF_MAX_K;
 constexpr int MAX_LLOYD = 20;
 constexpr int MAXG = 160;               // blocks of one group (one per SM)
-constexpr unsigned long long BARRIER_NS = 2000000000ull;
+constexpr unsigned long long DEFAULT_WAIT_NS = kDefaultWaitNs;
 constexpr float TIE_REL = 1.0f / 16384.0f;      // 2^-14: Lloyd recheck band
 constexpr float CAND_REL = 1.0f / 4096.0f;      // 2^-12: farthest-point candidates
 constexpr int TRACE_CAP = 2048;                  // trace events per launch
@@ -56,6 +53,7 @@ struct ClArgs {
   int p_bf16;         // guide stored as bfloat16
   int N, rho, K, G;   // G: blocks of the group that clusters this guide
   int bid;            // this block's rank in the group (set per block on the device)
+  unsigned long long wait_ns;   // limit of each device-side wait (set per launch)
   int* ctrl;
   float* mu;          // out: K x rho
   double* mu64;       // out: K x rho
@@ -93,7 +91,8 @@ size_t ws_bytes(int N, int rho, int G);   // workspace of one guide clustered by
 ClArgs make_args(void* ws, int N, int rho, int K, int G, int* ctrl, float* mu, double* mu64,
                  int32_t* labels, double* ek, const void* p, int p_bf16);
 cudaError_t launch_table(int rho_max, const ClArgs* table, const int4* groups, int ngroups,
-                         const int* order, const void* p_override, int grid, cudaStream_t st);
+                         const int* order, const void* p_override, int grid,
+                         unsigned long long wait_ns, cudaStream_t st);
 
 }  // namespace clus
 }  // namespace hdf

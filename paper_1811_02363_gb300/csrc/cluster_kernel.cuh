@@ -33,7 +33,8 @@
 // are kept in a planar copy permuted with the clusters, so every pass reads
 // them coalesced.
 //
-// Synchronisation: a grid barrier with a bounded wait (2 s), after which the
+// Synchronisation: a grid barrier with a bounded wait (2 s unless the launch
+// sets another limit), after which the
 // device status records HDF_ETIMEOUT and every block returns.  Reductions
 // across blocks are replayed identically by every block from the per-block
 // partial results, so block-local copies of the control state agree.
@@ -41,12 +42,40 @@
 
 #include <math.h>
 
+#include <type_traits>
+
 #include "cluster_args.cuh"
 
 namespace hdf {
 
 namespace clus {
 namespace {
+
+// Threads per block of this translation unit's instantiation (one block per
+// SM): the instantiations for guides of few dimensions keep few coordinates
+// per point in registers and run 32 warps per SM; those for many dimensions
+// run fewer, larger threads.  A chunk is CH points, PPT per thread.
+#ifndef HDF_CL_THREADS
+#define HDF_CL_THREADS 256
+#endif
+constexpr int CL_THREADS = HDF_CL_THREADS;
+constexpr int CL_WARPS = CL_THREADS / 32;
+constexpr int PPT = CH / CL_THREADS;    // points per thread per chunk
+static_assert(PPT * CL_THREADS == CH && PPT >= 1, "a chunk is a whole number of points per thread");
+// Wide blocks (few coordinates per point) take the Lloyd pass's chunks in
+// groups of CG of one segment, so that a thread has 8 points' loads in
+// flight; narrow blocks (many coordinates per point) compact each chunk's
+// points that need the full test so that their coordinate loads coalesce.
+constexpr bool COMPACT = CL_THREADS <= 512;
+constexpr int CG = COMPACT ? 1 : (8 / PPT > 1 ? 8 / PPT : 1);
+
+// Points whose coordinates one thread loads together (registers permitting).
+template <int RMAX>
+__host__ __device__ constexpr int load_batch() {
+  return (RMAX <= 4 ? 8 : (RMAX <= 8 ? 4 : (RMAX <= 32 ? 2 : 1))) < PPT
+             ? (RMAX <= 4 ? 8 : (RMAX <= 8 ? 4 : (RMAX <= 32 ? 2 : 1)))
+             : PPT;
+}
 
 struct ClShared {
   int seg_start[MAXSEG], seg_count[MAXSEG], seg_chunk0[MAXSEG + 1], seg_on[MAXSEG];
@@ -65,7 +94,7 @@ struct ClShared {
   double redD[CL_WARPS];
   int redx[CL_WARPS];
   int scanw[CL_WARPS];
-  int hlist[CH];          // positions of a chunk that need the full test
+  int hlist[COMPACT ? CH : 1];   // positions of a chunk that need the full test (COMPACT)
   int wtab[PPT * CL_WARPS];   // per (u, warp) counts, then their exclusive prefix
   int wtotal;
   float segmax[MAXSEG];
@@ -147,7 +176,7 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
 // Grid barrier with a bounded wait.  One monotonically growing arrival
 // counter per launch: the gen-th barrier is passed once it reaches gen * G,
 // so a block arrives with a single atomic and nobody resets anything.  The
-// wait gives up after BARRIER_NS (recording HDF_ETIMEOUT), or as soon as the
+// wait gives up after a.wait_ns (recording HDF_ETIMEOUT), or as soon as the
 // device status records an error from another block.  Returns false if the
 // device status records an error, in which case the caller returns.
 __device__ bool grid_barrier(const ClArgs& a, unsigned& gen, ClShared& s, int phase) {
@@ -164,7 +193,7 @@ __device__ bool grid_barrier(const ClArgs& a, unsigned& gen, ClShared& s, int ph
       while (ld_acquire_gpu(cnt) < target) {
         if ((++k & 31u) == 0) {
           if (*(volatile int*)(a.ctrl + CTRL_ERROR) != 0) break;
-          if (globaltimer_ns() - t0 > BARRIER_NS) {
+          if (globaltimer_ns() - t0 > a.wait_ns) {
             record_error(a.ctrl, HDF_ETIMEOUT);
             break;
           }
@@ -325,6 +354,32 @@ __device__ void for_blocks(const ClArgs& a, const ClShared& s, F f, Flush flush)
     f(seg, base, s.seg_start[seg] + s.seg_count[seg], j);
   }
   if (cur >= 0) flush(cur);
+}
+
+// The same iteration in groups: f(seg, bases, j0, end) takes up to CG chunks
+// j0, j0 + G, ... of one segment at once (bases[g] = first position of chunk
+// j0 + g G, -1 past the block's last chunk of the segment), so that the
+// loads of all of them can be issued together; flush(seg) once per segment
+// after its last chunk in this block.
+template <int NG, class F, class Flush>
+__device__ void for_block_groups(const ClArgs& a, const ClShared& s, F f, Flush flush) {
+  int seg = 0;
+  for (int j = a.bid; j < s.nchunks;) {
+    while (s.seg_chunk0[seg + 1] <= j) ++seg;
+    const int c0 = s.seg_chunk0[seg], cend = s.seg_chunk0[seg + 1];
+    const int start = s.seg_start[seg];
+    int bases[NG];
+    int ng = 0;
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      const int jj = j + g * a.G;
+      bases[g] = jj < cend ? start + (jj - c0) * CH : -1;
+      ng += jj < cend ? 1 : 0;
+    }
+    f(seg, bases, j, start + s.seg_count[seg]);
+    j += ng * a.G;
+    if (j >= cend) flush(seg);
+  }
 }
 
 // Blocks whose partial results cover segment `seg`, in a fixed order.
@@ -626,7 +681,7 @@ __device__ __noinline__ bool dist_stats_fn(const ClArgs& a, ClShared& s, unsigne
                                            const float* c32, const double* c64, float* X,
                                            const float* Xn, uint32_t* P, const uint32_t* Pn,
                                            bool from_scratch) {
-  constexpr int UB = RMAX <= 4 ? 8 : (RMAX <= 8 ? 4 : (RMAX <= 32 ? 2 : 1));
+  constexpr int UB = load_batch<RMAX>();
   const int rho = a.rho;
   const int PS = record_floats(rho);
   const int tid = threadIdx.x, bid = a.bid;
@@ -636,65 +691,68 @@ __device__ __noinline__ bool dist_stats_fn(const ClArgs& a, ClShared& s, unsigne
     float mx = -1.0f;
     F2 sse{0.0f, 0.0f};
     int seg_first_chunk = -1;
-    for_blocks(a, s,
-        [&](int seg, int base, int end, int j) {
-          if (seg_first_chunk < 0) seg_first_chunk = j;
-          const float* c = c32 + seg * rho;
+    // distances of a batch of points of segment seg (positions >= end skipped)
+    auto visit = [&](int seg, auto& posv, int end) {
+      constexpr int NB = std::extent<std::remove_reference_t<decltype(posv)>>::value;
+      const float* c = c32 + seg * rho;
+      float x[NB][RMAX];
+      uint32_t pid[NB];
+      const float* src = from_scratch ? Xn : X;
 #pragma unroll
-          for (int u0 = 0; u0 < PPT; u0 += UB) {
-            float x[UB][RMAX];
-            uint32_t pid[UB];
-            const float* src = from_scratch ? Xn : X;
+      for (int b = 0; b < NB; ++b) {
+        const int pos = posv[b];
+        const bool v = pos < end;
+        pid[b] = (v && from_scratch) ? __ldcg(Pn + pos) : 0u;
 #pragma unroll
-            for (int b = 0; b < UB; ++b) {
-              const int pos = base + (u0 + b) * CL_THREADS + tid;
-              const bool v = pos < end;
-              pid[b] = (v && from_scratch) ? __ldcg(Pn + pos) : 0u;
+        for (int d = 0; d < RMAX; ++d)
+          x[b][d] = (v && d < rho) ? __ldcg(src + (size_t)d * N + pos) : 0.0f;
+      }
 #pragma unroll
-              for (int d = 0; d < RMAX; ++d)
-                x[b][d] = (v && d < rho) ? __ldcg(src + (size_t)d * N + pos) : 0.0f;
-            }
+      for (int b = 0; b < NB; ++b) {
+        const int pos = posv[b];
+        if (pos >= end) continue;
+        float d2 = 0.0f;
 #pragma unroll
-            for (int b = 0; b < UB; ++b) {
-              const int pos = base + (u0 + b) * CL_THREADS + tid;
-              if (pos >= end) continue;
-              float d2 = 0.0f;
-#pragma unroll
-              for (int d = 0; d < RMAX; ++d) {
-                if (d < rho) {
-                  if (from_scratch) X[(size_t)d * N + pos] = x[b][d];
-                  const float t = x[b][d] - c[d];
-                  d2 = fmaf(t, t, d2);
-                }
-              }
-              if (from_scratch) P[pos] = pid[b];
-              a.d32[pos] = d2;
-              mx = fmaxf(mx, d2);
-              two_sum_acc(sse.hi, sse.lo, d2);
-            }
+        for (int d = 0; d < RMAX; ++d) {
+          if (d < rho) {
+            if (from_scratch) X[(size_t)d * N + pos] = x[b][d];
+            const float t = x[b][d] - c[d];
+            d2 = fmaf(t, t, d2);
           }
-        },
-        [&](int seg) {
+        }
+        if (from_scratch) P[pos] = pid[b];
+        a.d32[pos] = d2;
+        mx = fmaxf(mx, d2);
+        two_sum_acc(sse.hi, sse.lo, d2);
+      }
+    };
+    auto dflush = [&](int seg) {
           const size_t off = (size_t)bid * MAXSEG + seg;
           block_max_sum(mx, sse, s, a.pd + off, a.pf + off * PS);   // ends with a block sync
           const float m = s.bmax;                                   // this block's maximum
           // FP64 candidates of this block's chunks of the segment
           double bd = -1.0;
           int bi = 0x7fffffff;
-          for (int j = seg_first_chunk; j < s.seg_chunk0[seg + 1]; j += a.G) {
-            const int base = s.seg_start[seg] + (j - s.seg_chunk0[seg]) * CH;
-            const int end = s.seg_start[seg] + s.seg_count[seg];
-            float dd[PPT];
+          const int c1 = s.seg_chunk0[seg + 1];
+          const int end = s.seg_start[seg] + s.seg_count[seg];
+          for (int j = seg_first_chunk; j < c1; j += CG * a.G) {   // CG chunks' loads at once
+            constexpr int NQ = CG * PPT;
+            float dd[NQ];
+            int pp[NQ];
 #pragma unroll
-            for (int u = 0; u < PPT; ++u) {
-              const int pos = base + u * CL_THREADS + tid;
-              dd[u] = (pos < end) ? __ldcg(a.d32 + pos) : -1.0f;
+            for (int q = 0; q < NQ; ++q) {
+              const int jj = j + (q / PPT) * a.G;
+              const int pos = jj < c1 ? s.seg_start[seg] + (jj - s.seg_chunk0[seg]) * CH +
+                                            (q % PPT) * CL_THREADS + tid
+                                      : end;
+              pp[q] = pos;
+              dd[q] = (pos < end) ? __ldcg(a.d32 + pos) : -1.0f;
             }
 #pragma unroll
-            for (int u = 0; u < PPT; ++u) {
-              const int pos = base + u * CL_THREADS + tid;
+            for (int q = 0; q < NQ; ++q) {
+              const int pos = pp[q];
               if (pos >= end) continue;
-              if (m > 0.0f && dd[u] < m * (1.0f - CAND_REL)) continue;
+              if (m > 0.0f && dd[q] < m * (1.0f - CAND_REL)) continue;
               const int idx = (int)__ldcg(P + pos);
               double e = 0.0;
               if (m > 0.0f) {
@@ -717,7 +775,40 @@ __device__ __noinline__ bool dist_stats_fn(const ClArgs& a, ClShared& s, unsigne
           mx = -1.0f;
           sse = F2{0.0f, 0.0f};
           seg_first_chunk = -1;
-        });
+    };
+    if constexpr (COMPACT) {
+      for_blocks(a, s,
+          [&](int seg, int base, int end, int j) {
+            if (seg_first_chunk < 0) seg_first_chunk = j;
+#pragma unroll
+            for (int u0 = 0; u0 < PPT; u0 += UB) {
+              int pv[UB];
+#pragma unroll
+              for (int b2 = 0; b2 < UB; ++b2) pv[b2] = base + (u0 + b2) * CL_THREADS + tid;
+              visit(seg, pv, end);
+            }
+          },
+          dflush);
+    } else {
+      constexpr int NQ = CG * PPT;
+      constexpr int UBG = RMAX <= 4 ? (NQ < 8 ? NQ : 8) : (NQ < 4 ? NQ : 4);
+      static_assert(NQ % UBG == 0, "batches divide the group");
+      for_block_groups<CG>(a, s,
+          [&](int seg, const int (&bases)[CG], int j0, int end) {
+            if (seg_first_chunk < 0) seg_first_chunk = j0;
+#pragma unroll
+            for (int q0 = 0; q0 < NQ; q0 += UBG) {
+              int pv[UBG];
+#pragma unroll
+              for (int b2 = 0; b2 < UBG; ++b2) {
+                const int q = q0 + b2, g = q / PPT, u = q % PPT;
+                pv[b2] = bases[g] >= 0 ? bases[g] + u * CL_THREADS + tid : end;
+              }
+              visit(seg, pv, end);
+            }
+          },
+          dflush);
+    }
   }
   trace_event(a.trace, a.bid, s.tr_n, TR_DPASS);
   if (!grid_barrier(a, gen, s, TR_DIST1)) return false;
@@ -823,7 +914,7 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
   uint32_t* const Pn = a.perm2;
   int nnodes = 1, rounds = 0, lloyd_max = 0;
   // points whose coordinates are loaded together (registers permitting)
-  constexpr int UB = RMAX <= 4 ? 8 : (RMAX <= 8 ? 4 : (RMAX <= 32 ? 2 : 1));
+  constexpr int UB = load_batch<RMAX>();
   static_assert(PPT % UB == 0, "load batch must divide the points per thread");
   static_assert(PPT * CL_WARPS == 64, "the partition's prefix runs over 64 (u, warp) counts");
 
@@ -1025,7 +1116,7 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
           while (ld_acquire_gpu(a.arrive + sl) < need) {
             if ((++k & 31u) == 0) {
               if (*(volatile int*)(a.ctrl + CTRL_ERROR) != 0) { ok = 0; break; }
-              if (globaltimer_ns() - t0 > BARRIER_NS) {
+              if (globaltimer_ns() - t0 > a.wait_ns) {
                 record_error(a.ctrl, HDF_ETIMEOUT);
                 ok = 0;
                 break;
@@ -1054,10 +1145,12 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
         bulk_copy_g2s(dst + (size_t)c * PS, a.pf + off * PS, bytes, &s.mbar);
       }
       if (tid == 0) {
-        int ok = mbar_wait(&s.mbar, s.mb_phase, BARRIER_NS);
+        int ok = mbar_wait(&s.mbar, s.mb_phase, a.wait_ns);
         if (!ok) {
           record_error(a.ctrl, HDF_ETIMEOUT);
-          mbar_wait(&s.mbar, s.mb_phase, BARRIER_NS);   // let the copies in flight land
+          // let the copies in flight land before the block can leave (the
+          // default limit, however short the configured one is)
+          mbar_wait(&s.mbar, s.mb_phase, DEFAULT_WAIT_NS);
         }
         s.mb_phase ^= 1u;
         s.last = ok;
@@ -1201,106 +1294,143 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
         int cnt = 0, chg = 0;
 #pragma unroll
         for (int d = 0; d < RMAX; ++d) hi[d] = lo[d] = 0.0f;
-        for_blocks(a, s,
-            [&](int seg, int base, int end, int) {
-              // fast path: the assignment cannot change while the margin bound
-              // (stored margin minus the centre movement since) is positive
-              const float cum = (float)s.cum[seg];
-              bool heavy[PPT];
+        // The assignment cannot change while the margin bound (stored margin
+        // minus the centre movement since it was computed) is positive.
+        auto needs_test = [&](int seg, int pos, int end) -> bool {
+          const float cum = (float)s.cum[seg];
+          const float m0 = (pos < end && it > 0) ? __ldcg(a.marg + pos) : -1.0f;
+          return pos < end && !(m0 - cum > 1e-6f * (fabsf(m0) + cum));
+        };
+        // The full test of one point of split seg with coordinates x: nearer
+        // centre (FP64 within 2^-14 of a tie), new margin, side change, sums.
+        auto test_point = [&](int seg, int pos, const float (&x)[RMAX]) {
+          const float cum = (float)s.cum[seg];
+          const float* ca = c32 + (2 * seg) * rho;
+          const float* cb = ca + rho;
+          float da = 0.0f, db = 0.0f;
 #pragma unroll
-              for (int u = 0; u < PPT; ++u) {
-                const int pos = base + u * CL_THREADS + tid;
-                const float m0 = (pos < end && it > 0) ? __ldcg(a.marg + pos) : -1.0f;
-                heavy[u] = pos < end && !(m0 - cum > 1e-6f * (fabsf(m0) + cum));
+          for (int d = 0; d < RMAX; ++d) {
+            if (d < rho) {
+              const float ta = x[d] - ca[d], tb = x[d] - cb[d];
+              da = fmaf(ta, ta, da);
+              db = fmaf(tb, tb, db);
+            }
+          }
+          bool sd = db < da;
+          if (fabsf(da - db) <= TIE_REL * (da + db)) {
+            const double* ea = c64 + (2 * seg) * rho;
+            const double* eb = ea + rho;
+            double e_a = 0.0, e_b = 0.0;
+#pragma unroll
+            for (int d = 0; d < RMAX; ++d) {
+              if (d < rho) {
+                const double xd = (double)x[d];
+                e_a = fma(xd - ea[d], xd - ea[d], e_a);
+                e_b = fma(xd - eb[d], xd - eb[d], e_b);
               }
-              // compact the chunk's heavy points in position order (coalesced
-              // loads where they are dense) and spread them over the block
-              int hr[PPT];
-              const int nheavy = position_ranks(heavy, hr, s);
+            }
+            sd = e_b < e_a;
+          }
+          const float ra = sqrtf(da), rb = sqrtf(db);
+          a.marg[pos] = fabsf(rb - ra) - MARGIN_REL * (ra + rb) - s.cabs[seg] + cum;
+          const int sdp = (it > 0) ? (int)__ldcg(a.side + pos) : -1;
+          if ((int)sd != sdp) {
+            a.side[pos] = (uint8_t)sd;
+            a.side[N + pos] = (uint8_t)(it + 1);   // iteration of the last change
+          }
+          if (it == 0) {
+            if (sd) {
+              ++cnt;
 #pragma unroll
-              for (int u = 0; u < PPT; ++u)
-                if (heavy[u]) s.hlist[hr[u]] = base + u * CL_THREADS + tid;
-              __syncthreads();
-              const float* ca = c32 + (2 * seg) * rho;
-              const float* cb = ca + rho;
-              for (int q0 = 0; q0 < nheavy; q0 += UB * CL_THREADS) {
-                int hp[UB];
-                float x[UB][RMAX];
+              for (int d = 0; d < RMAX; ++d)
+                if (d < rho) two_sum_acc(hi[d], lo[d], x[d]);
+            }
+          } else if ((int)sd != sdp) {
+            ++chg;
+            cnt += sd ? 1 : -1;
 #pragma unroll
-                for (int b = 0; b < UB; ++b) {
-                  const int q = q0 + b * CL_THREADS + tid;
-                  hp[b] = q < nheavy ? s.hlist[q] : -1;
+            for (int d = 0; d < RMAX; ++d)
+              if (d < rho) two_sum_acc(hi[d], lo[d], sd ? x[d] : -x[d]);
+          }
+        };
+        auto flush_split = [&](int seg) {
+          const size_t off = (size_t)bid * MAXSEG + seg;
+          if (__syncthreads_or(cnt != 0 || chg != 0)) {
+            block_sum_f2<RMAX>(hi, lo, rho, s, a.pf + off * PS);
+            block_sum_i2(cnt, chg, s, reinterpret_cast<int*>(a.pf + off * PS + 2 * rho));
+          } else {   // nothing moved to or from side b here: a zero record
+            for (int v = tid; v < PS; v += CL_THREADS) a.pf[off * PS + v] = 0.0f;
+          }
 #pragma unroll
-                  for (int d = 0; d < RMAX; ++d)
-                    x[b][d] = (hp[b] >= 0 && d < rho) ? xat(X, N, d, hp[b]) : 0.0f;
-                }
+          for (int d = 0; d < RMAX; ++d) hi[d] = lo[d] = 0.0f;
+          cnt = 0;
+          chg = 0;
+          arrive(seg);
+        };
+        if constexpr (COMPACT) {
+          // compact each chunk's points that need the full test in position
+          // order (coalesced coordinate loads where they are dense) and spread
+          // them over the block
+          for_blocks(a, s,
+              [&](int seg, int base, int end, int) {
+                bool heavy[PPT];
 #pragma unroll
-                for (int b = 0; b < UB; ++b) {
-                  if (hp[b] < 0) continue;
-                  const int pos = hp[b];
-                  float da = 0.0f, db = 0.0f;
+                for (int u = 0; u < PPT; ++u) heavy[u] = needs_test(seg, base + u * CL_THREADS + tid, end);
+                int hr[PPT];
+                const int nheavy = position_ranks(heavy, hr, s);
 #pragma unroll
-                  for (int d = 0; d < RMAX; ++d) {
-                    if (d < rho) {
-                      const float ta = x[b][d] - ca[d], tb = x[b][d] - cb[d];
-                      da = fmaf(ta, ta, da);
-                      db = fmaf(tb, tb, db);
-                    }
-                  }
-                  bool sd = db < da;
-                  if (fabsf(da - db) <= TIE_REL * (da + db)) {
-                    const double* ea = c64 + (2 * seg) * rho;
-                    const double* eb = ea + rho;
-                    double e_a = 0.0, e_b = 0.0;
+                for (int u = 0; u < PPT; ++u)
+                  if (heavy[u]) s.hlist[hr[u]] = base + u * CL_THREADS + tid;
+                __syncthreads();
+                for (int q0 = 0; q0 < nheavy; q0 += UB * CL_THREADS) {
+                  int hp[UB];
+                  float x[UB][RMAX];
 #pragma unroll
-                    for (int d = 0; d < RMAX; ++d) {
-                      if (d < rho) {
-                        const double xd = (double)x[b][d];
-                        e_a = fma(xd - ea[d], xd - ea[d], e_a);
-                        e_b = fma(xd - eb[d], xd - eb[d], e_b);
-                      }
-                    }
-                    sd = e_b < e_a;
-                  }
-                  const float ra = sqrtf(da), rb = sqrtf(db);
-                  a.marg[pos] = fabsf(rb - ra) - MARGIN_REL * (ra + rb) - s.cabs[seg] + cum;
-                  const int sdp = (it > 0) ? (int)__ldcg(a.side + pos) : -1;
-                  if ((int)sd != sdp) {
-                    a.side[pos] = (uint8_t)sd;
-                    a.side[N + pos] = (uint8_t)(it + 1);   // iteration of the last change
-                  }
-                  if (it == 0) {
-                    if (sd) {
-                      ++cnt;
-#pragma unroll
-                      for (int d = 0; d < RMAX; ++d)
-                        if (d < rho) two_sum_acc(hi[d], lo[d], x[b][d]);
-                    }
-                  } else if ((int)sd != sdp) {
-                    ++chg;
-                    cnt += sd ? 1 : -1;
+                  for (int b = 0; b < UB; ++b) {
+                    const int q = q0 + b * CL_THREADS + tid;
+                    hp[b] = q < nheavy ? s.hlist[q] : -1;
 #pragma unroll
                     for (int d = 0; d < RMAX; ++d)
-                      if (d < rho) two_sum_acc(hi[d], lo[d], sd ? x[b][d] : -x[b][d]);
+                      x[b][d] = (hp[b] >= 0 && d < rho) ? xat(X, N, d, hp[b]) : 0.0f;
                   }
-                }
-              }
-              __syncthreads();   // hlist is reused by the next chunk
-            },
-            [&](int seg) {
-              const size_t off = (size_t)bid * MAXSEG + seg;
-              if (__syncthreads_or(cnt != 0 || chg != 0)) {
-                block_sum_f2<RMAX>(hi, lo, rho, s, a.pf + off * PS);
-                block_sum_i2(cnt, chg, s, reinterpret_cast<int*>(a.pf + off * PS + 2 * rho));
-              } else {   // nothing moved to or from side b here: a zero record
-                for (int v = tid; v < PS; v += CL_THREADS) a.pf[off * PS + v] = 0.0f;
-              }
 #pragma unroll
-              for (int d = 0; d < RMAX; ++d) hi[d] = lo[d] = 0.0f;
-              cnt = 0;
-              chg = 0;
-              arrive(seg);
-            });
+                  for (int b = 0; b < UB; ++b)
+                    if (hp[b] >= 0) test_point(seg, hp[b], x[b]);
+                }
+                __syncthreads();   // hlist is reused by the next chunk
+              },
+              flush_split);
+        } else {
+          // each thread tests its own points of CG chunks at once: no block
+          // barrier inside the pass, all margin loads of the group in flight
+          constexpr int NQ = CG * PPT;
+          constexpr int UBG = RMAX <= 4 ? (NQ < 8 ? NQ : 8) : (NQ < 4 ? NQ : 4);
+          static_assert(NQ % UBG == 0, "coordinate batches divide the group");
+          for_block_groups<CG>(a, s,
+              [&](int seg, const int (&bases)[CG], int, int end) {
+                int hp[NQ];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                  const int g = q / PPT, u = q % PPT;
+                  const int pos = bases[g] >= 0 ? bases[g] + u * CL_THREADS + tid : end;
+                  hp[q] = needs_test(seg, pos, end) ? pos : -1;
+                }
+#pragma unroll
+                for (int q0 = 0; q0 < NQ; q0 += UBG) {
+                  float x[UBG][RMAX];
+#pragma unroll
+                  for (int b = 0; b < UBG; ++b) {
+#pragma unroll
+                    for (int d = 0; d < RMAX; ++d)
+                      x[b][d] = (hp[q0 + b] >= 0 && d < rho) ? xat(X, N, d, hp[q0 + b]) : 0.0f;
+                  }
+#pragma unroll
+                  for (int b = 0; b < UBG; ++b)
+                    if (hp[q0 + b] >= 0) test_point(seg, hp[q0 + b], x[b]);
+                }
+              },
+              flush_split);
+        }
       }
       // finish the splits this block is the finishing block of
       for (int sl = 0; sl < s.nslots; ++sl) {
@@ -1570,7 +1700,8 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
 template <int RMAX>
 __global__ void __launch_bounds__(CL_THREADS, 1)
 cluster_kernel(const ClArgs* __restrict__ table, const int4* __restrict__ groups, int ngroups,
-               const int* __restrict__ order, const void* p_override) {
+               const int* __restrict__ order, const void* p_override,
+               unsigned long long wait_ns) {
   __shared__ ClShared s;
   __shared__ ClArgs sa;
   __shared__ int4 s_grp;
@@ -1590,6 +1721,7 @@ cluster_kernel(const ClArgs* __restrict__ table, const int4* __restrict__ groups
     if (threadIdx.x == 0) {
       sa = table[order[t]];
       sa.bid = (int)blockIdx.x - gr.x;
+      sa.wait_ns = wait_ns;
       if (p_override) sa.p = p_override;
     }
     __syncthreads();
@@ -1601,7 +1733,8 @@ cluster_kernel(const ClArgs* __restrict__ table, const int4* __restrict__ groups
 // Host: cooperative launch of one instantiation over `grid` blocks.
 template <int RMAX>
 cudaError_t launch_cl(const ClArgs* table, const int4* groups, int ngroups, const int* order,
-                      const void* p_override, int rho_max, int grid, cudaStream_t st) {
+                      const void* p_override, int rho_max, int grid, unsigned long long wait_ns,
+                      cudaStream_t st) {
   const size_t smem = dyn_smem_bytes(rho_max);
   cudaError_t e = cudaFuncSetAttribute(cluster_kernel<RMAX>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1621,7 +1754,8 @@ cudaError_t launch_cl(const ClArgs* table, const int4* groups, int ngroups, cons
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, cluster_kernel<RMAX>, table, groups, ngroups, order, p_override);
+  return cudaLaunchKernelEx(&cfg, cluster_kernel<RMAX>, table, groups, ngroups, order, p_override,
+                            wait_ns);
 }
 
 }  // namespace

@@ -12,6 +12,13 @@
 namespace hdf {
 
 constexpr float kGuardRel = 1e-6f;   // guard: sum_k c_k r_k <= 1e-6 max_k r_k
+// The float32 denominator sum_k c_k r_k carries a rounding of a few units of
+// 2^-24 times sum_k |c_k| r_k.  Where that sum exceeds kIllCond times
+// |sum_k c_k r_k| (cancellation: the float32 value of g_hat may be off by more
+// than 1e-4), or the guard's threshold lies within kNearBand times it (the
+// float32 decision may go either way), the pixel is recomputed in FP64.
+constexpr float kIllCond = 64.0f;
+constexpr float kNearBand = 1.0f / 262144.0f;   // 2^-18
 
 // Shared-memory tables of the range-map kernels: the centres transposed,
 // smu[d][k], and A^+ by rows, spi[k][l], both with rows of KP = K rounded up
@@ -114,12 +121,26 @@ __device__ __forceinline__ void rangemap_pixel(const GT* __restrict__ p, size_t 
 
 // Eq. (15)-(16): g_hat = (sum_k c_k v_k) / (sum_k c_k r_k) at one pixel, the
 // numerators already in g.  A pixel failing the guard is appended to
-// fix_list (count in ctrl[CTRL_FALLBACK]) for the indicator fix-up.
+// fix_list (count in ctrl[CTRL_FALLBACK]) for the indicator fix-up.  With
+// dabs (sum_k |c_k| r_k per pixel) given, a pixel whose float32 denominator
+// is ill-conditioned or within rounding of the guard's threshold is instead
+// appended, from the end, to the same list (count in ctrl[CTRL_RESCUED]) for
+// the FP64 recomputation; a pixel is in at most one of the two parts.
 __device__ __forceinline__ void divide_pixel(float* __restrict__ g, const float* __restrict__ den,
                                              const float* __restrict__ rmax, int* ctrl,
-                                             int* __restrict__ fix_list, int N, int n, int pix) {
+                                             int* __restrict__ fix_list, int N, int n, int pix,
+                                             const float* __restrict__ dabs = nullptr) {
   const float D = den[pix];
-  if (!(D > kGuardRel * rmax[pix])) {
+  const float thr = kGuardRel * rmax[pix];
+  if (dabs) {
+    const float Ab = dabs[pix];
+    if (!(Ab <= kIllCond * fabsf(D)) || fabsf(D - thr) <= kNearBand * Ab) {
+      const int pos = atomicAdd(ctrl + CTRL_RESCUED, 1);
+      if (pos < N) fix_list[N - 1 - pos] = pix;
+      return;
+    }
+  }
+  if (!(D > thr)) {
     const int pos = atomicAdd(ctrl + CTRL_FALLBACK, 1);
     if (pos < N) fix_list[pos] = pix;
     return;

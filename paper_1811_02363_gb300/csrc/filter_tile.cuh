@@ -17,7 +17,9 @@
 // 512 threads; each thread owns YV consecutive rows of one column of one
 // plane for the whole k loop.  Outputs: the numerator planes (unnormalised)
 // into g, and for the chunk holding plane 0 the denominator and max_k r_k
-// into per-pixel scratch, normalised afterwards by the divide kernel.
+// into per-pixel scratch, normalised afterwards by the divide kernel; also
+// sum_k |c_k| r_k, the scale of the denominator's rounding (the divide kernel
+// hands pixels whose denominator is ill-conditioned to an FP64 recomputation).
 #pragma once
 
 #include "hdf_internal.cuh"
@@ -31,6 +33,7 @@ struct FilterArgs {
   float* g;             // (n, H, W) numerator sum_k c_k v_k (normalised later)
   float* den;           // (H, W) sum_k c_k r_k
   float* rmax;          // (H, W) max_k r_k
+  float* dabs;          // (H, W) sum_k |c_k| r_k, the rounding scale of the denominator (may be null)
   const int* ctrl;
   int H, W, n;
   int box, S;           // box spatial kernel (omega = 1 on W) of half-width S <= SB
@@ -77,7 +80,7 @@ struct TileCfg {
   static constexpr int SBF = HR * LD;
   static constexpr int SH = P * HR * LDH;
   static constexpr int SR = TY * TX;
-  static constexpr size_t SMEM = sizeof(float) * (size_t)(SF + 2 * SBF + SH + SR);
+  static constexpr size_t SMEM = sizeof(float) * (size_t)(SF + 2 * SBF + SH + 2 * SR);
   static_assert(TY % YV == 0 && YV >= 1, "tile height must be a multiple of the per-thread run");
   static_assert(TX * (TY / YV) * P == NT, "one column run per thread");
   static_assert(LD >= HC, "row stride must hold the halo");
@@ -187,6 +190,7 @@ filter_tile_kernel(const FilterArgs a, const Taps taps) {
   float* sB0 = sF + Cfg::SF;             // [2][HR][LD] b_k, double-buffered
   float* sH = sB0 + 2 * Cfg::SBF;        // [P][HR][LDH] row-pass results
   float* sR = sH + Cfg::SH;              // [TY][TX] max_k r_k (plane 0 only)
+  float* sA = sR + Cfg::SR;              // [TY][TX] sum_k |c_k| r_k (plane 0 only)
 
   const int tid = threadIdx.x;
   const int H = a.H, W = a.W, n = a.n;
@@ -259,7 +263,7 @@ filter_tile_kernel(const FilterArgs a, const Taps taps) {
   auto stage_b = [&](int k, float* dst) { stage_rows(a.B + (size_t)k * N, dst, warp, HR); };
   stage_b(0, sB0);
   cp_async_commit();
-  for (int i = tid; i < Cfg::SR; i += NT) sR[i] = 0.0f;
+  for (int i = tid; i < 2 * Cfg::SR; i += NT) sR[i] = 0.0f;   // sR and sA
 
   float acc[YV], cnext[YV];
   // c_k at this thread's pixels: rows yv0 .. yv0 + YV - 1 of column gx
@@ -352,6 +356,8 @@ filter_tile_kernel(const FilterArgs a, const Taps taps) {
         for (int o = 0; o < YV; ++o) {
           float* pr = sR + (yv0 + o) * TX + xv;
           *pr = fmaxf(*pr, v[o]);
+          float* pa = sA + (yv0 + o) * TX + xv;
+          *pa = fmaf(fabsf(ccur[o]), v[o], *pa);
         }
       }
     }
@@ -366,6 +372,7 @@ filter_tile_kernel(const FilterArgs a, const Taps taps) {
         if (qgv == 0) {
           a.den[pix] = acc[o];
           a.rmax[pix] = sR[(yv0 + o) * TX + xv];
+          if (a.dabs) a.dabs[pix] = sA[(yv0 + o) * TX + xv];
         } else {
           a.g[(size_t)(qgv - 1) * N + pix] = acc[o];
         }

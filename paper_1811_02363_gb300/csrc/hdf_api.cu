@@ -100,39 +100,44 @@ hdf_status hdf_create(hdf_handle** out, const hdf_desc* desc) {
   memset(h, 0, sizeof(*h));
   h->d = d;
   h->N = d.H * d.W;
+  h->wait_ns = hdf::kDefaultWaitNs;
   HDF_CUDA(cudaGetDevice(&h->device), "cudaGetDevice");
   const size_t N = (size_t)h->N, K = (size_t)d.K, R = (size_t)d.rho;
   bool ok = true;
-  ok &= dalloc(&h->ctrl, hdf::CTRL_WORDS) == cudaSuccess;
-  ok &= dalloc(&h->mu, K * R) == cudaSuccess;
-  ok &= dalloc(&h->mu64, K * R) == cudaSuccess;
-  ok &= dalloc(&h->pinv64, K * K) == cudaSuccess;
-  ok &= dalloc(&h->pinv32, K * K) == cudaSuccess;
-  ok &= dalloc(&h->ek, 1) == cudaSuccess;
-  ok &= dalloc(&h->B, K * N) == cudaSuccess;
-  ok &= dalloc(&h->C, K * N) == cudaSuccess;
-  ok &= dalloc(&h->s, N) == cudaSuccess;
-  ok &= dalloc(&h->den, N) == cudaSuccess;
-  ok &= dalloc(&h->rmax, N) == cudaSuccess;
-  ok &= dalloc(&h->fix_list, N) == cudaSuccess;
-  ok &= dalloc(&h->grad_scratch, 1 << 16) == cudaSuccess;
-  ok &= dalloc(&h->labels, N) == cudaSuccess;
-  ok &= dalloc(&h->bw_g, (size_t)d.n * N) == cudaSuccess;
-  ok &= dalloc(&h->bw_lam, (size_t)(d.n + 1) * N) == cudaSuccess;
-  ok &= dalloc(&h->bw_gam, K * N) == cudaSuccess;
-  ok &= dalloc(&h->bw_bet, K * N) == cudaSuccess;
-  ok &= dalloc(&h->bw_flag, N) == cudaSuccess;
+  // stop at the first allocation that fails (nothing more is attempted)
+  auto take = [&](auto** p, size_t count) {
+    if (ok) ok = dalloc(p, count) == cudaSuccess;
+  };
+  take(&h->ctrl, hdf::CTRL_WORDS);
+  take(&h->mu, K * R);
+  take(&h->mu64, K * R);
+  take(&h->pinv64, K * K);
+  take(&h->pinv32, K * K);
+  take(&h->ek, 1);
+  take(&h->B, K * N);
+  take(&h->C, K * N);
+  take(&h->s, N);
+  take(&h->den, N);
+  take(&h->rmax, N);
+  take(&h->dabs, N);
+  take(&h->fix_list, N);
+  take(&h->grad_scratch, 1 << 16);
+  take(&h->labels, N);
+  take(&h->bw_g, (size_t)d.n * N);
+  take(&h->bw_lam, (size_t)(d.n + 1) * N);
+  take(&h->bw_gam, K * N);
+  take(&h->bw_bet, K * N);
+  take(&h->bw_flag, N);
   h->young_T = nullptr;
-  if (d.spatial == HDF_SPATIAL_YOUNG)
-    ok &= dalloc(&h->young_T, K * (size_t)(d.n + 1) * N) == cudaSuccess;
+  if (d.spatial == HDF_SPATIAL_YOUNG) take(&h->young_T, K * (size_t)(d.n + 1) * N);
   {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     h->nlm_ws_bytes = hdf::nlm_workspace_bytes(sms > 0 ? sms : 1);
   }
-  ok &= cudaMalloc(&h->nlm_ws, h->nlm_ws_bytes) == cudaSuccess;
+  if (ok) ok = cudaMalloc(&h->nlm_ws, h->nlm_ws_bytes) == cudaSuccess;
   h->cl_ws_bytes = hdf::cluster_workspace_bytes(h->N, d.rho, d.K);
-  ok &= cudaMalloc(&h->cl_ws, h->cl_ws_bytes) == cudaSuccess;
+  if (ok) ok = cudaMalloc(&h->cl_ws, h->cl_ws_bytes) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     hdf_destroy(h);
@@ -152,6 +157,8 @@ hdf_status hdf_create(hdf_handle** out, const hdf_desc* desc) {
 void hdf_destroy(hdf_handle* h) {
   if (!h) return;
   cudaDeviceSynchronize();
+  for (int i = 0; i < 4; ++i)
+    if (h->tev[i]) cudaEventDestroy(h->tev[i]);
   cudaFree(h->ctrl);
   cudaFree(h->mu);
   cudaFree(h->mu64);
@@ -163,6 +170,7 @@ void hdf_destroy(hdf_handle* h) {
   cudaFree(h->s);
   cudaFree(h->den);
   cudaFree(h->rmax);
+  cudaFree(h->dabs);
   cudaFree(h->fix_list);
   cudaFree(h->grad_scratch);
   cudaFree(h->labels);
@@ -177,6 +185,33 @@ void hdf_destroy(hdf_handle* h) {
   delete h;
 }
 
+hdf_status hdf_set_stage_timing(hdf_handle* h, int on) {
+  if (!h) return HDF_EINVAL;
+  if (on && !h->tev[0]) {
+    for (int i = 0; i < 4; ++i) HDF_CUDA(cudaEventCreate(&h->tev[i]), "timing events");
+  }
+  h->timing = on ? 1 : 0;
+  return HDF_OK;
+}
+
+hdf_status hdf_get_stage_times(hdf_handle* h, float* h_ms, int cap, int* count) {
+  if (!h || !h_ms || !count || cap < 0) return HDF_EINVAL;
+  *count = 0;
+  if (!h->tev[0]) return HDF_EINVAL;
+  HDF_CUDA(cudaEventSynchronize(h->tev[3]), "timing sync");
+  for (int i = 0; i < 3 && i < cap; ++i) {
+    HDF_CUDA(cudaEventElapsedTime(h_ms + i, h->tev[i], h->tev[i + 1]), "timing elapsed");
+    *count = i + 1;
+  }
+  return HDF_OK;
+}
+
+hdf_status hdf_set_wait_limit(hdf_handle* h, double seconds) {
+  if (!h || !(seconds >= 0.0) || !(seconds <= 60.0)) return HDF_EINVAL;
+  h->wait_ns = (unsigned long long)(seconds * 1e9);
+  return HDF_OK;
+}
+
 hdf_status hdf_get_desc(const hdf_handle* h, hdf_desc* out) {
   if (!h || !out) return HDF_EINVAL;
   *out = h->d;
@@ -186,7 +221,11 @@ hdf_status hdf_get_desc(const hdf_handle* h, hdf_desc* out) {
 hdf_status hdf_cluster(hdf_handle* h, const void* d_p, void* stream) {
   if (!h || !d_p) return HDF_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  HDF_CUDA(hdf::launch_cluster(h, d_p, st), "cluster");
+  {
+    hdf::NvtxRange r("hdf cluster: bisecting K-means");
+    HDF_CUDA(hdf::launch_cluster(h, d_p, st), "cluster");
+  }
+  hdf::NvtxRange r("hdf cluster: fit A, A^+");
   HDF_CUDA(hdf::launch_fit(h, st), "fit");
   return HDF_OK;
 }
@@ -237,8 +276,18 @@ hdf_status hdf_apply(hdf_handle* h, const float* d_f, const void* d_p, float* d_
   if (!h || !d_f || !d_p || !d_g) return HDF_EINVAL;
   if ((const void*)d_g == (const void*)d_f || (const void*)d_g == d_p) return HDF_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  HDF_CUDA(hdf::launch_rangemap(h, d_p, st), "rangemap");
-  HDF_CUDA(hdf::launch_filter(h, d_f, d_g, st), "filter");
+  if (h->timing) HDF_CUDA(cudaEventRecord(h->tev[0], st), "timing event");
+  {
+    hdf::NvtxRange r("hdf apply: range maps");
+    HDF_CUDA(hdf::launch_rangemap(h, d_p, st), "rangemap");
+  }
+  if (h->timing) {
+    HDF_CUDA(cudaEventRecord(h->tev[1], st), "timing event");
+    HDF_CUDA(cudaEventRecord(h->tev[2], st), "timing event");   // moved on by the tile kernel
+  }
+  hdf::NvtxRange r("hdf apply: convolutions + combine");
+  HDF_CUDA(hdf::launch_filter(h, d_f, d_p, d_g, st), "filter");
+  if (h->timing) HDF_CUDA(cudaEventRecord(h->tev[3], st), "timing event");
   return HDF_OK;
 }
 
@@ -247,6 +296,7 @@ hdf_status hdf_backward(hdf_handle* h, const float* d_f, const void* d_p, const 
   if (!h || !d_f || !d_p || !d_grad_g || !d_grad_f || !d_grad_log_sigma) return HDF_EINVAL;
   if (h->d.coef != HDF_COEF_OPT || h->d.spatial != HDF_SPATIAL_GAUSS) return HDF_EUNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
+  hdf::NvtxRange r("hdf backward");
   HDF_CUDA(hdf::launch_backward(h, d_f, d_p, d_grad_g, d_grad_f, d_grad_log_sigma, st),
            "backward");
   return HDF_OK;
@@ -257,6 +307,7 @@ hdf_status hdf_nlm_guide(hdf_handle* h, const float* d_f, int patch, float* d_p,
   const hdf_desc& d = h->d;
   if (d.n * patch * patch > 96 || d.n > 4 || d.rho > d.n * patch * patch) return HDF_EUNSUPPORTED;
   if (d.H < patch / 2 + 1 || d.W < patch / 2 + 1) return HDF_EINVAL;
+  hdf::NvtxRange r("hdf nlm guide");
   HDF_CUDA(hdf::launch_nlm_guide(d_f, d.n, d.H, d.W, patch, d.rho, d_p, h->nlm_ws, h->nlm_ws_bytes,
                                  h->ctrl, (cudaStream_t)stream),
            "nlm_guide");
@@ -269,6 +320,7 @@ hdf_status hdf_bruteforce(const hdf_desc* desc, const float* d_f, const void* d_
   hdf_desc d = *desc;
   hdf_status s = check_desc(&d);
   if (s != HDF_OK) return s;
+  hdf::NvtxRange r("hdf brute force");
   HDF_CUDA(hdf::launch_bruteforce(d, d_f, d_p, d_g, (cudaStream_t)stream), "bruteforce");
   return HDF_OK;
 }
@@ -289,7 +341,8 @@ hdf_status hdf_get_stats(hdf_handle* h, hdf_stats* out, void* stream) {
   HDF_CUDA(cudaStreamSynchronize(st), "sync");
   out->K_eff = c[hdf::CTRL_K_EFF];
   out->device_error = c[hdf::CTRL_ERROR];
-  out->fallback_pixels = c[hdf::CTRL_FALLBACK];
+  out->fallback_pixels = c[hdf::CTRL_FALLBACK] + c[hdf::CTRL_FALLBACK64];
+  out->rescued_pixels = c[hdf::CTRL_RESCUED];
   out->lloyd_iters_max = c[hdf::CTRL_LLOYD_MAX];
   out->rounds = c[hdf::CTRL_ROUNDS];
   out->cluster_error = ek;

@@ -392,7 +392,7 @@ cudaError_t enqueue(hdf_batch* b, int flags, cudaStream_t st, cudaEvent_t* ev) {
   mark(2);
   if (e == cudaSuccess && cluster)
     e = clus::launch_table(b->rho_max_cl, b->d_cl, b->d_grp, (int)b->groups.size(), b->d_ord,
-                           nullptr, b->grid_cluster, st);
+                           nullptr, b->grid_cluster, clus::DEFAULT_WAIT_NS, st);
   mark(3);
   if (e == cudaSuccess && cluster) e = launch_fit_batch(b->d_fit, ncl, b->Kmax, st);
   mark(4);
@@ -631,6 +631,7 @@ hdf_status hdf_batch_set_centers(hdf_batch* b, int i, const float* h_mu, int K) 
 
 hdf_status hdf_batch_run(hdf_batch* b, int flags, void* stream) {
   if (!b || !b->bound) return HDF_EINVAL;
+  hdf::NvtxRange r("hdf batch run");
   cudaStream_t user = (cudaStream_t)stream;
   const int key = flags & HDF_BATCH_SKIP_CLUSTER;
   if (flags & HDF_BATCH_TIMED) {
@@ -705,7 +706,8 @@ hdf_status hdf_batch_tune(hdf_batch* b, int reps, void* stream) {
       if (e == cudaSuccess) e = cudaEventRecord(e0, st);
       if (e == cudaSuccess)
         e = hdf::clus::launch_table(b->rho_max_cl, b->d_cl, b->d_grp, (int)b->groups.size(),
-                                    b->d_ord, nullptr, b->grid_cluster, st);
+                                    b->d_ord, nullptr, b->grid_cluster,
+                                    hdf::clus::DEFAULT_WAIT_NS, st);
       if (e == cudaSuccess) e = cudaEventRecord(e1, st);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       float t = 0.0f;
@@ -822,6 +824,7 @@ hdf_status hdf_batch_get_stats(hdf_batch* b, int i, hdf_stats* out) {
   out->lloyd_iters_max = c[hdf::CTRL_LLOYD_MAX];
   out->rounds = c[hdf::CTRL_ROUNDS];
   out->cluster_error = ek;
+  out->rescued_pixels = 0;   // the batch keeps every pixel on the float32 path
   return (hdf_status)c[hdf::CTRL_ERROR];
 }
 

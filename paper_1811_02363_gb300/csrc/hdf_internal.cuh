@@ -6,6 +6,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/hdfilter.h"
 
 namespace hdf {
@@ -18,10 +20,16 @@ enum CtrlSlot {
   CTRL_LLOYD_MAX = 3,    // largest 2-means iteration count of the last clustering
   CTRL_ROUNDS = 4,       // split rounds of the last clustering
   CTRL_RANKDEF = 5,      // 1 if the last fit dropped eigenvalues of A (truncated pseudo-inverse)
+  CTRL_RESCUED = 6,      // pixels of the last apply recomputed in FP64 (ill-conditioned denominator)
+  CTRL_FALLBACK64 = 7,   // of those, pixels that took the denominator guard
   CTRL_BARRIER = 8,      // grid barrier: arrival counter
   CTRL_BARRIER_GEN = 9,  // reserved (zeroed with the barrier counter)
   CTRL_WORDS = 16
 };
+
+// Default limit of every device-side wait (grid barriers, split finishers,
+// bulk-copy completion) before the kernel records HDF_ETIMEOUT and returns.
+constexpr unsigned long long kDefaultWaitNs = 2000000000ull;
 
 // Record `code` as the device error unless one is already recorded.
 __device__ __forceinline__ void record_error(int* ctrl, int code) {
@@ -54,6 +62,7 @@ struct hdf_handle {
   int N;              // H * W
   int device;         // CUDA device the buffers live on
   int* ctrl;          // CTRL_WORDS control words
+  unsigned long long wait_ns;   // limit of each device-side wait of the clustering
   float* mu;          // K x rho centres (float32, what the filter uses)
   double* mu64;       // K x rho centres before rounding (clustering means)
   double* pinv64;     // K x K A^+ (float64)
@@ -64,6 +73,7 @@ struct hdf_handle {
   uint8_t* s;         // N nearest centre (Voronoi cell) per pixel
   float* den;         // N denominator sum_k c_k r_k of the last apply
   float* rmax;        // N max_k r_k of the last apply (guard)
+  float* dabs;        // N sum_k |c_k| r_k of the last apply (rounding scale of the denominator)
   int* fix_list;      // N pixels that take the denominator guard
   double* grad_scratch;  // backward partial sums
   // clustering workspace (allocated in hdf_create, sized by N)
@@ -79,6 +89,10 @@ struct hdf_handle {
   float* young_T;     // K x (n+1) x N row-filtered planes (recursive Gaussian only)
   void* nlm_ws;       // NLM guide workspace
   size_t nlm_ws_bytes;
+  // stage timing of hdf_apply (hdf_set_stage_timing): events before the range
+  // maps, after them, after the convolution tile kernel, after the last stage
+  int timing;
+  cudaEvent_t tev[4];
 };
 
 namespace hdf {
@@ -98,8 +112,13 @@ cudaError_t launch_fit(hdf_handle* h, cudaStream_t st);           // A, A^+ from
 cudaError_t launch_fit_batch(const FitJob* jobs, int njobs, int Kmax, cudaStream_t st);
 cudaError_t launch_set_int(int* p, int v, cudaStream_t st);
 cudaError_t launch_rangemap(hdf_handle* h, const void* p, cudaStream_t st);
-cudaError_t launch_filter(hdf_handle* h, const float* f, float* g, cudaStream_t st);
+// rescue = 0: no FP64 recomputation of ill-conditioned pixels (the backward
+// pass's forward recomputation keeps every pixel on the float32 path).
+cudaError_t launch_filter(hdf_handle* h, const float* f, const void* p, float* g, cudaStream_t st,
+                          int rescue = 1);
 cudaError_t launch_young(hdf_handle* h, const float* f, float* g, cudaStream_t st);
+cudaError_t launch_rescue(hdf_handle* h, const float* f, const void* p, float* g, int* list,
+                          cudaStream_t st);   // FP64 recomputation of the listed pixels
 cudaError_t launch_bruteforce(const hdf_desc& d, const float* f, const void* p, float* g,
                               cudaStream_t st);
 cudaError_t cluster_init(hdf_handle* h);                          // one-entry table, at create
@@ -117,6 +136,15 @@ Taps make_taps(double sigma_s, int S, int spatial);   // omega_1 at [t + S], 0 b
 hdf_status cuda_fail(cudaError_t e, const char* where);   // records the text for hdf_last_cuda_error
 hdf_status check_desc(hdf_desc* d);                       // validates, fills S = ceil(3 sigma_s) if 0
 int filter_bucket(int S);                                 // compiled window bucket >= S, -1 if none
+
+// NVTX range over the host side of one stage (what a timeline tool shows
+// next to the kernels the stage enqueues).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 }  // namespace hdf
 

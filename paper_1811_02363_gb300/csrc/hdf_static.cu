@@ -28,8 +28,8 @@
 namespace {
 
 // Largest scratch one call may use: 32 MiB.  A call needs
-//   K*K*12 + 64 + H*W*(8*K + 13) bytes (plus alignment),
-// e.g. K = 32 at 256 x 256 pixels (17.6 MB) or K = 8 at 512 x 512 (21.2 MB).
+//   K*K*12 + 64 + H*W*(8*K + 17) bytes (plus alignment),
+// e.g. K = 32 at 256 x 256 pixels (17.9 MB) or K = 8 at 512 x 512 (21.2 MB).
 constexpr size_t kStaticScratchBytes = 32u << 20;
 constexpr int kMaxDevices = 64;
 
@@ -69,8 +69,9 @@ extern "C" hdf_status hdf_apply_static(const hdf_desc* desc, const float* d_mu, 
   if (d.spatial == HDF_SPATIAL_YOUNG) return HDF_EUNSUPPORTED;   // needs per-plane scratch
   const size_t N = (size_t)d.H * d.W;
 
-  // carve the scratch: control words, A^+ (f64, f32), B, C, s, den, rmax, guard list
-  size_t off = 0, o_ctrl, o_p64, o_p32, o_B, o_C, o_s, o_den, o_rmax, o_fix;
+  // carve the scratch: control words, A^+ (f64, f32), B, C, s, den, rmax,
+  // sum |c_k| r_k, guard list
+  size_t off = 0, o_ctrl, o_p64, o_p32, o_B, o_C, o_s, o_den, o_rmax, o_dabs, o_fix;
   o_ctrl = off; off = align256(off + sizeof(int) * hdf::CTRL_WORDS);
   o_p64 = off;  off = align256(off + sizeof(double) * K * K);
   o_p32 = off;  off = align256(off + sizeof(float) * K * K);
@@ -79,6 +80,7 @@ extern "C" hdf_status hdf_apply_static(const hdf_desc* desc, const float* d_mu, 
   o_s = off;    off = align256(off + N);
   o_den = off;  off = align256(off + sizeof(float) * N);
   o_rmax = off; off = align256(off + sizeof(float) * N);
+  o_dabs = off; off = align256(off + sizeof(float) * N);
   o_fix = off;  off = align256(off + sizeof(int) * N);
   if (off > kStaticScratchBytes) return HDF_EUNSUPPORTED;   // beyond the 32 MiB array
 
@@ -106,6 +108,7 @@ extern "C" hdf_status hdf_apply_static(const hdf_desc* desc, const float* d_mu, 
   h.s = (uint8_t*)(w + o_s);
   h.den = (float*)(w + o_den);
   h.rmax = (float*)(w + o_rmax);
+  h.dabs = (float*)(w + o_dabs);
   h.fix_list = (int*)(w + o_fix);
 
   // The previous call's contents stay in the array: clear the control words
@@ -114,6 +117,6 @@ extern "C" hdf_status hdf_apply_static(const hdf_desc* desc, const float* d_mu, 
   HDF_CUDA(hdf::launch_set_int(h.ctrl + hdf::CTRL_K_EFF, K, st_), "apply_static K");
   HDF_CUDA(hdf::launch_fit(&h, st_), "apply_static fit");
   HDF_CUDA(hdf::launch_rangemap(&h, d_p, st_), "apply_static rangemap");
-  HDF_CUDA(hdf::launch_filter(&h, d_f, d_g, st_), "apply_static filter");
+  HDF_CUDA(hdf::launch_filter(&h, d_f, d_p, d_g, st_), "apply_static filter");
   return HDF_OK;
 }

@@ -228,7 +228,7 @@ cudaError_t launch_backward(hdf_handle* h, const float* f, const void* p, const 
   if (ntiles > PART_SIGMA_R) return cudaErrorInvalidValue;   // per-tile partials must fit
   // 1. forward recompute (g_hat into scratch, D, guard list)
   if ((e = launch_rangemap(h, p, st)) != cudaSuccess) return e;
-  if ((e = launch_filter(h, f, h->bw_g, st)) != cudaSuccess) return e;
+  if ((e = launch_filter(h, f, p, h->bw_g, st, 0)) != cudaSuccess) return e;
   // 2. guarded pixels
   if ((e = cudaMemsetAsync(h->bw_flag, 0, h->N, st)) != cudaSuccess) return e;
   const Taps exact = make_taps(d.sigma_s, d.S, d.spatial);

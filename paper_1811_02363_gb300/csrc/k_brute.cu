@@ -1,13 +1,23 @@
 // Brute-force high-dimensional bilateral / NLM filter, Eq. (1)-(2):
-//   g(i) = sum_{j in W} omega(j) phi(p(i-j) - p(i)) f(i-j) / eta(i),
-// one thread per output pixel, the window's guide (and image, unless it
-// aliases the guide) staged in shared memory per tile when it fits, read
-// through the cache otherwise.  Neighbours outside the image are left out.
+//   g(i) = sum_{j in W} omega(j) phi(p(i-j) - p(i)) f(i-j) / eta(i).
+// Float32 guides of up to 32 dimensions take the register-blocked tile kernel
+// (brute_tile.cuh); the others (bfloat16 guides, more dimensions, the widest
+// bucket at 32 dimensions) take the kernel below: one thread per output pixel,
+// the window's guide (and image, unless it aliases the guide) staged in shared
+// memory per tile when it fits, read through the cache otherwise.  Neighbours
+// outside the image are left out.
 #include <math.h>
 
+#include "brute_tile.cuh"
 #include "hdf_internal.cuh"
 
 namespace hdf {
+
+cudaError_t launch_brute_tile_a(int maxc, int SB, const BruteTileArgs& a, const Taps& t,
+                                cudaStream_t st);
+cudaError_t launch_brute_tile_b(int maxc, int SB, const BruteTileArgs& a, const Taps& t,
+                                cudaStream_t st);
+
 namespace {
 
 struct BruteArgs {
@@ -143,6 +153,19 @@ cudaError_t launch_bruteforce(const hdf_desc& d, const float* f, const void* p, 
               (float)(1.0 / (2.0 * d.sigma_r * d.sigma_r))};
   const Taps taps = make_taps(d.sigma_s, d.S, d.spatial);
   if (d.guide_dtype == HDF_GUIDE_BF16) return launch_brute_c<__nv_bfloat16>(a, taps, st);
+  const int SB = filter_bucket(d.S);
+  const int c = d.n > d.rho ? d.n : d.rho;
+  const int maxc = c <= 4 ? 4 : c <= 8 ? 8 : c <= 16 ? 16 : c <= 32 ? 32 : 0;
+  if (SB > 0 && maxc > 0) {
+    // taps centred in the bucket: w[SB + j] = omega_1(j) for |j| <= S, 0 beyond
+    Taps tb;
+    for (int t = 0; t < 2 * HDF_MAX_S + 1; ++t) tb.w[t] = 0.0f;
+    for (int j = -d.S; j <= d.S; ++j) tb.w[SB + j] = taps.w[d.S + j];
+    BruteTileArgs bt{f, (const float*)p, g, d.H, d.W, d.n, d.rho, a.alias, a.inv2sr2};
+    const cudaError_t e = maxc <= 8 ? launch_brute_tile_a(maxc, SB, bt, tb, st)
+                                    : launch_brute_tile_b(maxc, SB, bt, tb, st);
+    if (e != cudaErrorNotSupported) return e;
+  }
   return launch_brute_c<float>(a, taps, st);
 }
 

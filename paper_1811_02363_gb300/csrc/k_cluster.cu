@@ -8,15 +8,20 @@
 namespace hdf {
 
 cudaError_t launch_cluster_r4(const clus::ClArgs*, const int4*, int, const int*, const void*, int,
-                              int, cudaStream_t);
+                              int, unsigned long long,
+                               cudaStream_t);
 cudaError_t launch_cluster_r8(const clus::ClArgs*, const int4*, int, const int*, const void*, int,
-                              int, cudaStream_t);
+                              int, unsigned long long,
+                               cudaStream_t);
 cudaError_t launch_cluster_r16(const clus::ClArgs*, const int4*, int, const int*, const void*,
-                               int, int, cudaStream_t);
+                               int, int, unsigned long long,
+                               cudaStream_t);
 cudaError_t launch_cluster_r32(const clus::ClArgs*, const int4*, int, const int*, const void*,
-                               int, int, cudaStream_t);
+                               int, int, unsigned long long,
+                               cudaStream_t);
 cudaError_t launch_cluster_r64(const clus::ClArgs*, const int4*, int, const int*, const void*,
-                               int, int, cudaStream_t);
+                               int, int, unsigned long long,
+                               cudaStream_t);
 
 namespace clus {
 namespace {
@@ -114,16 +119,17 @@ ClArgs make_args(void* ws, int N, int rho, int K, int G, int* ctrl, float* mu, d
 }
 
 cudaError_t launch_table(int rho_max, const ClArgs* table, const int4* groups, int ngroups,
-                         const int* order, const void* p_override, int grid, cudaStream_t st) {
+                         const int* order, const void* p_override, int grid,
+                         unsigned long long wait_ns, cudaStream_t st) {
   if (rho_max <= 4)
-    return launch_cluster_r4(table, groups, ngroups, order, p_override, rho_max, grid, st);
+    return launch_cluster_r4(table, groups, ngroups, order, p_override, rho_max, grid, wait_ns, st);
   if (rho_max <= 8)
-    return launch_cluster_r8(table, groups, ngroups, order, p_override, rho_max, grid, st);
+    return launch_cluster_r8(table, groups, ngroups, order, p_override, rho_max, grid, wait_ns, st);
   if (rho_max <= 16)
-    return launch_cluster_r16(table, groups, ngroups, order, p_override, rho_max, grid, st);
+    return launch_cluster_r16(table, groups, ngroups, order, p_override, rho_max, grid, wait_ns, st);
   if (rho_max <= 32)
-    return launch_cluster_r32(table, groups, ngroups, order, p_override, rho_max, grid, st);
-  return launch_cluster_r64(table, groups, ngroups, order, p_override, rho_max, grid, st);
+    return launch_cluster_r32(table, groups, ngroups, order, p_override, rho_max, grid, wait_ns, st);
+  return launch_cluster_r64(table, groups, ngroups, order, p_override, rho_max, grid, wait_ns, st);
 }
 
 }  // namespace clus
@@ -168,7 +174,8 @@ cudaError_t launch_cluster(hdf_handle* h, const void* p, cudaStream_t st) {
   e = cudaMemsetAsync(w + L.trace, 0, sizeof(long long), st);
   if (e != cudaSuccess) return e;
   return clus::launch_table(h->d.rho, (const clus::ClArgs*)(w + L.tab),
-                            (const int4*)(w + L.grp), 1, (const int*)(w + L.ord), p, G, st);
+                            (const int4*)(w + L.grp), 1, (const int*)(w + L.ord), p, G,
+                            h->wait_ns, st);
 }
 
 cudaError_t cluster_trace(hdf_handle* h, long long* host, int cap, int* count, cudaStream_t st) {

@@ -5,8 +5,8 @@ namespace hdf {
 
 cudaError_t launch_cluster_r64(const clus::ClArgs* table, const int4* groups, int ngroups,
                               const int* order, const void* p_override, int rho_max, int grid,
-                              cudaStream_t st) {
-  return clus::launch_cl<64>(table, groups, ngroups, order, p_override, rho_max, grid, st);
+                              unsigned long long wait_ns, cudaStream_t st) {
+  return clus::launch_cl<64>(table, groups, ngroups, order, p_override, rho_max, grid, wait_ns, st);
 }
 
 }  // namespace hdf

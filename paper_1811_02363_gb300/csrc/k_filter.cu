@@ -67,10 +67,10 @@ __global__ void fixup_kernel(const float* __restrict__ f, const float* __restric
 
 // Eq. (15)-(16) normalisation with the denominator guard (combine.cuh).
 __global__ void divide_kernel(float* __restrict__ g, const float* __restrict__ den,
-                              const float* __restrict__ rmax, int* __restrict__ ctrl,
-                              int* __restrict__ fix_list, int N, int n) {
+                              const float* __restrict__ rmax, const float* __restrict__ dabs,
+                              int* __restrict__ ctrl, int* __restrict__ fix_list, int N, int n) {
   for (int pix = blockIdx.x * blockDim.x + threadIdx.x; pix < N; pix += gridDim.x * blockDim.x)
-    divide_pixel(g, den, rmax, ctrl, fix_list, N, n, pix);
+    divide_pixel(g, den, rmax, ctrl, fix_list, N, n, pix, dabs);
 }
 
 }  // namespace
@@ -93,7 +93,8 @@ int filter_bucket(int S) {
   return -1;
 }
 
-cudaError_t launch_filter(hdf_handle* h, const float* f, float* g, cudaStream_t st) {
+cudaError_t launch_filter(hdf_handle* h, const float* f, const void* p, float* g, cudaStream_t st,
+                          int rescue) {
   const hdf_desc& d = h->d;
   if (d.spatial == HDF_SPATIAL_YOUNG) return launch_young(h, f, g, st);
   const int SB = filter_bucket(d.S);
@@ -106,18 +107,24 @@ cudaError_t launch_filter(hdf_handle* h, const float* f, float* g, cudaStream_t 
   for (int j = -d.S; j <= d.S; ++j) taps.w[SB + j] = exact.w[d.S + j];
   cudaError_t e = cudaMemsetAsync(h->ctrl + CTRL_FALLBACK, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  FilterArgs a{f, h->B, h->C, g, h->den, h->rmax, h->ctrl, d.H, d.W, d.n,
+  e = cudaMemsetAsync(h->ctrl + CTRL_RESCUED, 0, 2 * sizeof(int), st);   // and CTRL_FALLBACK64
+  if (e != cudaSuccess) return e;
+  float* dabs = rescue ? h->dabs : nullptr;
+  FilterArgs a{f, h->B, h->C, g, h->den, h->rmax, dabs, h->ctrl, d.H, d.W, d.n,
                d.spatial == HDF_SPATIAL_BOX ? 1 : 0, d.S,
                (d.W % 4 == 0 && reinterpret_cast<uintptr_t>(f) % 16 == 0) ? 1 : 0};
   e = launch_filter_sb(SB, P, a, taps, st);
   if (e != cudaSuccess) return e;
+  if (h->timing && rescue && (e = cudaEventRecord(h->tev[2], st)) != cudaSuccess) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  divide_kernel<<<sms * 4, 256, 0, st>>>(g, h->den, h->rmax, h->ctrl, h->fix_list, h->N, d.n);
+  divide_kernel<<<sms * 4, 256, 0, st>>>(g, h->den, h->rmax, dabs, h->ctrl, h->fix_list, h->N, d.n);
   fixup_kernel<<<sms, 256, 0, st>>>(f, h->B, h->s, h->fix_list, h->ctrl, d.H, d.W, d.n, d.S,
                                     exact, g);
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess || !rescue) return e;
+  return launch_rescue(h, f, p, g, h->fix_list, st);   // ill-conditioned pixels, in FP64
 }
 
 }  // namespace hdf

@@ -101,6 +101,22 @@ def smooth_field_with_edges(H: int, W: int, noise: float = 0.1, n_edges: int = 8
     return field[None].astype(np.float32)
 
 
+def lowlight_infrared(H: int, W: int, seed: int = 5) -> tuple[np.ndarray, np.ndarray]:
+    """A dark, noisy grayscale frame and a registered infrared frame of the
+    same scene (stand-in for the low-light + infrared pair of Sec. III-E):
+    the scene is ``smooth_field_with_edges`` without noise; the low-light
+    frame is 0.15 x scene + N(0, 0.02^2) noise; the infrared frame is
+    0.6 x scene + 0.2 x an independent smooth texture (low-pass 8 px) +
+    N(0, 0.005^2) noise, clipped to [0, 1].  Returns two float32 (1, H, W)."""
+    rng = np.random.default_rng(seed)
+    scene = smooth_field_with_edges(H, W, noise=0.0, seed=seed + 1000)[0].astype(np.float64)
+    dark = 0.15 * scene + rng.normal(0.0, 0.02, size=(H, W))
+    tex = _lowpass_wrap(rng.uniform(0.0, 1.0, size=(H, W)), 8.0)
+    tex = (tex - tex.min()) / max(tex.max() - tex.min(), 1e-12)
+    ir = np.clip(0.6 * scene + 0.2 * tex + rng.normal(0.0, 0.005, size=(H, W)), 0.0, 1.0)
+    return dark[None].astype(np.float32), ir[None].astype(np.float32)
+
+
 @dataclasses.dataclass
 class BatchItem:
     """One image of the batched serving workload with its filter parameters."""

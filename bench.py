@@ -49,7 +49,7 @@ EXTRA_CONFIGS = ["color256", "hyper512", "nlm1024"]
 METRIC = "megapixels/s of the fast filter (cluster + fit + filter) on one GB300"
 UNIT = "MP/s"
 L2_FLUSH_BYTES = 256 << 20          # larger than the 129 MB L2
-CPU_CROP = 256                      # crop side of the oracle baseline sample
+CPU_CROP = 768                      # crop side of the oracle baseline sample (~5 s on one core)
 REF_STEP_CROP = 128                 # crop side of one reference-arm step
 SAMPLED_PIXELS = 24                 # oracle pixels per configuration (plus the 4 corners)
 

@@ -16,6 +16,8 @@ defined.
 """
 from __future__ import annotations
 
+import math
+
 import torch
 
 
@@ -76,4 +78,43 @@ def grads(f, p, mu, sigma_s: float, sigma_r: float, S: int, G):
     g = fast_filter_torch(f, pt, mu, ls, lr, S)
     L = (g * torch.tensor(G, dtype=torch.float64)).sum()
     L.backward()
+    return f.grad.numpy(), float(ls.grad), float(lr.grad), g.detach().numpy()
+
+
+def bruteforce_torch(f: torch.Tensor, p: torch.Tensor | None, log_sigma_s: torch.Tensor,
+                     log_sigma_r: torch.Tensor, S: int) -> torch.Tensor:
+    """Eq. (1)-(2) in float64 torch, differentiable in f, log sigma_s and log
+    sigma_r: g(i) = sum_j omega(j) phi(p(i-j) - p(i)) f(i-j) / eta(i) over
+    W = [-S, S]^2, neighbours outside the image left out.  p=None: p = f."""
+    p = f if p is None else p
+    n, H, W = f.shape
+    ss, sr = torch.exp(log_sigma_s), torch.exp(log_sigma_r)
+    num = torch.zeros_like(f)
+    den = torch.zeros_like(f[0])
+    for j1 in range(-S, S + 1):
+        for j2 in range(-S, S + 1):
+            y0, y1 = max(0, j1), min(H, H + j1)
+            x0, x1 = max(0, j2), min(W, W + j2)
+            if y0 >= y1 or x0 >= x1:
+                continue
+            w = torch.exp(-torch.tensor(float(j1 * j1 + j2 * j2), dtype=torch.float64)
+                          / (2.0 * ss * ss))
+            pi = p[:, y0:y1, x0:x1]
+            pn = p[:, y0 - j1:y1 - j1, x0 - j2:x1 - j2]
+            wt = w * torch.exp(-((pn - pi) ** 2).sum(dim=0) / (2.0 * sr * sr))
+            pad = (x0, W - x1, y0, H - y1)
+            num = num + torch.nn.functional.pad(wt * f[:, y0 - j1:y1 - j1, x0 - j2:x1 - j2], pad)
+            den = den + torch.nn.functional.pad(wt, pad)
+    return num / den
+
+
+def brute_grads(f, p, sigma_s: float, sigma_r: float, S: int, G):
+    """dL/df, dL/dlog sigma_s, dL/dlog sigma_r of L = <G, g> for the brute
+    force (float64 autograd); p=None means guide = image."""
+    f = torch.tensor(f, dtype=torch.float64, requires_grad=True)
+    pt = None if p is None else torch.tensor(p, dtype=torch.float64)
+    ls = torch.tensor(math.log(sigma_s), dtype=torch.float64, requires_grad=True)
+    lr = torch.tensor(math.log(sigma_r), dtype=torch.float64, requires_grad=True)
+    g = bruteforce_torch(f, pt, ls, lr, S)
+    (g * torch.tensor(G, dtype=torch.float64)).sum().backward()
     return f.grad.numpy(), float(ls.grad), float(lr.grad), g.detach().numpy()

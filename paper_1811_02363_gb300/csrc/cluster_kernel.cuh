@@ -62,12 +62,6 @@ constexpr int CL_THREADS = HDF_CL_THREADS;
 constexpr int CL_WARPS = CL_THREADS / 32;
 constexpr int PPT = CH / CL_THREADS;    // points per thread per chunk
 static_assert(PPT * CL_THREADS == CH && PPT >= 1, "a chunk is a whole number of points per thread");
-// Wide blocks (few coordinates per point) take the Lloyd pass's chunks in
-// groups of CG of one segment, so that a thread has 8 points' loads in
-// flight; narrow blocks (many coordinates per point) compact each chunk's
-// points that need the full test so that their coordinate loads coalesce.
-constexpr bool COMPACT = CL_THREADS <= 512;
-constexpr int CG = COMPACT ? 1 : (8 / PPT > 1 ? 8 / PPT : 1);
 
 // Points whose coordinates one thread loads together (registers permitting).
 template <int RMAX>
@@ -79,6 +73,7 @@ __host__ __device__ constexpr int load_batch() {
 
 struct ClShared {
   int seg_start[MAXSEG], seg_count[MAXSEG], seg_chunk0[MAXSEG + 1], seg_on[MAXSEG];
+  int seg_act[MAXSEG];    // splits still iterating (the Lloyd loop keeps its chunk table)
   int nseg, nchunks;
   SlotRec slot[MAXACT];
   int nslots;
@@ -94,7 +89,7 @@ struct ClShared {
   double redD[CL_WARPS];
   int redx[CL_WARPS];
   int scanw[CL_WARPS];
-  int hlist[COMPACT ? CH : 1];   // positions of a chunk that need the full test (COMPACT)
+  int hlist[CH];          // positions of a chunk that need the full test
   int wtab[PPT * CL_WARPS];   // per (u, warp) counts, then their exclusive prefix
   int wtotal;
   float segmax[MAXSEG];
@@ -354,32 +349,6 @@ __device__ void for_blocks(const ClArgs& a, const ClShared& s, F f, Flush flush)
     f(seg, base, s.seg_start[seg] + s.seg_count[seg], j);
   }
   if (cur >= 0) flush(cur);
-}
-
-// The same iteration in groups: f(seg, bases, j0, end) takes up to CG chunks
-// j0, j0 + G, ... of one segment at once (bases[g] = first position of chunk
-// j0 + g G, -1 past the block's last chunk of the segment), so that the
-// loads of all of them can be issued together; flush(seg) once per segment
-// after its last chunk in this block.
-template <int NG, class F, class Flush>
-__device__ void for_block_groups(const ClArgs& a, const ClShared& s, F f, Flush flush) {
-  int seg = 0;
-  for (int j = a.bid; j < s.nchunks;) {
-    while (s.seg_chunk0[seg + 1] <= j) ++seg;
-    const int c0 = s.seg_chunk0[seg], cend = s.seg_chunk0[seg + 1];
-    const int start = s.seg_start[seg];
-    int bases[NG];
-    int ng = 0;
-#pragma unroll
-    for (int g = 0; g < NG; ++g) {
-      const int jj = j + g * a.G;
-      bases[g] = jj < cend ? start + (jj - c0) * CH : -1;
-      ng += jj < cend ? 1 : 0;
-    }
-    f(seg, bases, j, start + s.seg_count[seg]);
-    j += ng * a.G;
-    if (j >= cend) flush(seg);
-  }
 }
 
 // Blocks whose partial results cover segment `seg`, in a fixed order.
@@ -735,8 +704,8 @@ __device__ __noinline__ bool dist_stats_fn(const ClArgs& a, ClShared& s, unsigne
           int bi = 0x7fffffff;
           const int c1 = s.seg_chunk0[seg + 1];
           const int end = s.seg_start[seg] + s.seg_count[seg];
-          for (int j = seg_first_chunk; j < c1; j += CG * a.G) {   // CG chunks' loads at once
-            constexpr int NQ = CG * PPT;
+          for (int j = seg_first_chunk; j < c1; j += a.G) {
+            constexpr int NQ = PPT;
             float dd[NQ];
             int pp[NQ];
 #pragma unroll
@@ -776,39 +745,18 @@ __device__ __noinline__ bool dist_stats_fn(const ClArgs& a, ClShared& s, unsigne
           sse = F2{0.0f, 0.0f};
           seg_first_chunk = -1;
     };
-    if constexpr (COMPACT) {
-      for_blocks(a, s,
-          [&](int seg, int base, int end, int j) {
-            if (seg_first_chunk < 0) seg_first_chunk = j;
+    for_blocks(a, s,
+        [&](int seg, int base, int end, int j) {
+          if (seg_first_chunk < 0) seg_first_chunk = j;
 #pragma unroll
-            for (int u0 = 0; u0 < PPT; u0 += UB) {
-              int pv[UB];
+          for (int u0 = 0; u0 < PPT; u0 += UB) {
+            int pv[UB];
 #pragma unroll
-              for (int b2 = 0; b2 < UB; ++b2) pv[b2] = base + (u0 + b2) * CL_THREADS + tid;
-              visit(seg, pv, end);
-            }
-          },
-          dflush);
-    } else {
-      constexpr int NQ = CG * PPT;
-      constexpr int UBG = RMAX <= 4 ? (NQ < 8 ? NQ : 8) : (NQ < 4 ? NQ : 4);
-      static_assert(NQ % UBG == 0, "batches divide the group");
-      for_block_groups<CG>(a, s,
-          [&](int seg, const int (&bases)[CG], int j0, int end) {
-            if (seg_first_chunk < 0) seg_first_chunk = j0;
-#pragma unroll
-            for (int q0 = 0; q0 < NQ; q0 += UBG) {
-              int pv[UBG];
-#pragma unroll
-              for (int b2 = 0; b2 < UBG; ++b2) {
-                const int q = q0 + b2, g = q / PPT, u = q % PPT;
-                pv[b2] = bases[g] >= 0 ? bases[g] + u * CL_THREADS + tid : end;
-              }
-              visit(seg, pv, end);
-            }
-          },
-          dflush);
-    }
+            for (int b2 = 0; b2 < UB; ++b2) pv[b2] = base + (u0 + b2) * CL_THREADS + tid;
+            visit(seg, pv, end);
+          }
+        },
+        dflush);
   }
   trace_event(a.trace, a.bid, s.tr_n, TR_DPASS);
   if (!grid_barrier(a, gen, s, TR_DIST1)) return false;
@@ -1094,7 +1042,9 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
       }
     }
     __syncthreads();
-    build_chunks(s);
+    build_chunks(s);   // the chunk table of the whole Lloyd loop: a block keeps its points
+    if (tid < s.nslots) s.seg_act[tid] = !s.slot[tid].done;
+    __syncthreads();
 
     // Arrival of this block's partial sums of split sl (written by the block
     // before the barrier): one release-add, nobody waits for it.
@@ -1354,6 +1304,7 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
           }
         };
         auto flush_split = [&](int seg) {
+          if (!s.seg_act[seg]) return;   // converged split: no record, no arrival
           const size_t off = (size_t)bid * MAXSEG + seg;
           if (__syncthreads_or(cnt != 0 || chg != 0)) {
             block_sum_f2<RMAX>(hi, lo, rho, s, a.pf + off * PS);
@@ -1367,74 +1318,43 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
           chg = 0;
           arrive(seg);
         };
-        if constexpr (COMPACT) {
-          // compact each chunk's points that need the full test in position
-          // order (coalesced coordinate loads where they are dense) and spread
-          // them over the block
-          for_blocks(a, s,
-              [&](int seg, int base, int end, int) {
-                bool heavy[PPT];
+        // compact each chunk's points that need the full test in position
+        // order (coalesced coordinate loads where they are dense) and spread
+        // them over the block
+        for_blocks(a, s,
+            [&](int seg, int base, int end, int) {
+              if (!s.seg_act[seg]) return;   // uniform: shared flag
+              bool heavy[PPT];
 #pragma unroll
-                for (int u = 0; u < PPT; ++u) heavy[u] = needs_test(seg, base + u * CL_THREADS + tid, end);
-                int hr[PPT];
-                const int nheavy = position_ranks(heavy, hr, s);
+              for (int u = 0; u < PPT; ++u) heavy[u] = needs_test(seg, base + u * CL_THREADS + tid, end);
+              int hr[PPT];
+              const int nheavy = position_ranks(heavy, hr, s);
 #pragma unroll
-                for (int u = 0; u < PPT; ++u)
-                  if (heavy[u]) s.hlist[hr[u]] = base + u * CL_THREADS + tid;
-                __syncthreads();
-                for (int q0 = 0; q0 < nheavy; q0 += UB * CL_THREADS) {
-                  int hp[UB];
-                  float x[UB][RMAX];
+              for (int u = 0; u < PPT; ++u)
+                if (heavy[u]) s.hlist[hr[u]] = base + u * CL_THREADS + tid;
+              __syncthreads();
+              for (int q0 = 0; q0 < nheavy; q0 += UB * CL_THREADS) {
+                int hp[UB];
+                float x[UB][RMAX];
 #pragma unroll
-                  for (int b = 0; b < UB; ++b) {
-                    const int q = q0 + b * CL_THREADS + tid;
-                    hp[b] = q < nheavy ? s.hlist[q] : -1;
+                for (int b = 0; b < UB; ++b) {
+                  const int q = q0 + b * CL_THREADS + tid;
+                  hp[b] = q < nheavy ? s.hlist[q] : -1;
 #pragma unroll
-                    for (int d = 0; d < RMAX; ++d)
-                      x[b][d] = (hp[b] >= 0 && d < rho) ? xat(X, N, d, hp[b]) : 0.0f;
-                  }
-#pragma unroll
-                  for (int b = 0; b < UB; ++b)
-                    if (hp[b] >= 0) test_point(seg, hp[b], x[b]);
-                }
-                __syncthreads();   // hlist is reused by the next chunk
-              },
-              flush_split);
-        } else {
-          // each thread tests its own points of CG chunks at once: no block
-          // barrier inside the pass, all margin loads of the group in flight
-          constexpr int NQ = CG * PPT;
-          constexpr int UBG = RMAX <= 4 ? (NQ < 8 ? NQ : 8) : (NQ < 4 ? NQ : 4);
-          static_assert(NQ % UBG == 0, "coordinate batches divide the group");
-          for_block_groups<CG>(a, s,
-              [&](int seg, const int (&bases)[CG], int, int end) {
-                int hp[NQ];
-#pragma unroll
-                for (int q = 0; q < NQ; ++q) {
-                  const int g = q / PPT, u = q % PPT;
-                  const int pos = bases[g] >= 0 ? bases[g] + u * CL_THREADS + tid : end;
-                  hp[q] = needs_test(seg, pos, end) ? pos : -1;
+                  for (int d = 0; d < RMAX; ++d)
+                    x[b][d] = (hp[b] >= 0 && d < rho) ? xat(X, N, d, hp[b]) : 0.0f;
                 }
 #pragma unroll
-                for (int q0 = 0; q0 < NQ; q0 += UBG) {
-                  float x[UBG][RMAX];
-#pragma unroll
-                  for (int b = 0; b < UBG; ++b) {
-#pragma unroll
-                    for (int d = 0; d < RMAX; ++d)
-                      x[b][d] = (hp[q0 + b] >= 0 && d < rho) ? xat(X, N, d, hp[q0 + b]) : 0.0f;
-                  }
-#pragma unroll
-                  for (int b = 0; b < UBG; ++b)
-                    if (hp[q0 + b] >= 0) test_point(seg, hp[q0 + b], x[b]);
-                }
-              },
-              flush_split);
-        }
+                for (int b = 0; b < UB; ++b)
+                  if (hp[b] >= 0) test_point(seg, hp[b], x[b]);
+              }
+              __syncthreads();   // hlist is reused by the next chunk
+            },
+            flush_split);
       }
       // finish the splits this block is the finishing block of
       for (int sl = 0; sl < s.nslots; ++sl) {
-        if (!s.seg_on[sl] || finisher_of(sl) != bid) continue;
+        if (!s.seg_act[sl] || finisher_of(sl) != bid) continue;
         if (!wait_arrivals(sl)) return;
         trace_event(a.trace, a.bid, s.tr_n, TR_FWAIT);
         if (!finish_split(sl, it)) return;
@@ -1445,12 +1365,12 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
       // every block takes the published state of the splits that were active
       for (int v = tid; v < s.nslots * 3 * rho; v += CL_THREADS) {
         const int i = v / (3 * rho), r = v % (3 * rho);
-        if (!s.seg_on[i]) continue;
+        if (!s.seg_act[i]) continue;
         if (r < 2 * rho) c64[2 * i * rho + r] = __ldcg(a.gcen + (size_t)i * 2 * rho + r);
         else acc_sum[i * rho + r - 2 * rho] = __ldcg(a.gacc + (size_t)i * rho + r - 2 * rho);
       }
       for (int i = tid; i < s.nslots; i += CL_THREADS) {
-        if (!s.seg_on[i]) continue;
+        if (!s.seg_act[i]) continue;
         const SlotOut* o = a.sout + i;
         SlotRec& sl = s.slot[i];
         sl.done = __ldcg(&o->r.done);
@@ -1466,11 +1386,10 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
       }
       __syncthreads();
       for (int v = tid; v < s.nslots * 2 * rho; v += CL_THREADS)
-        if (s.seg_on[v / (2 * rho)]) c32[v] = (float)c64[v];
+        if (s.seg_act[v / (2 * rho)]) c32[v] = (float)c64[v];
       __syncthreads();
-      if (tid < s.nslots) s.seg_on[tid] = !s.slot[tid].done;
+      if (tid < s.nslots) s.seg_act[tid] = !s.slot[tid].done;
       __syncthreads();
-      build_chunks(s);
       trace_event(a.trace, a.bid, s.tr_n, TR_LUPDATE);
     }
     if (tid == 0) {

@@ -1,5 +1,5 @@
 // Clustering kernel instantiated for guides of up to 8 dimensions.
-#define HDF_CL_THREADS 1024   // threads per block of this instantiation
+#define HDF_CL_THREADS 512   // threads per block of this instantiation
 #include "cluster_kernel.cuh"
 
 namespace hdf {

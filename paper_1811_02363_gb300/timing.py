@@ -1,12 +1,12 @@
 """Stage timings of the named synthetic workloads on the current GPU.
 
 For each workload: the PCA guide (nonlocal means), the clustering, the filter
-apply with the Gaussian, box and recursive-Gaussian spatial kernels, and with
---backward the gradient pass (dL/df, dL/dlog sigma_s, dL/dlog sigma_r) of the
+apply with the Gaussian, box and recursive-Gaussian spatial kernels, with
+--bruteforce the brute force of Eq. (1)-(2), and with --backward the gradient pass (dL/df, dL/dlog sigma_s, dL/dlog sigma_r) of the
 Gaussian filter for a random upstream gradient.  Times are medians of CUDA
 events on the current stream, inputs resident on the device.
 
-    python -m paper_1811_02363_gb300.timing hyper512 color2048 --backward
+    python -m paper_1811_02363_gb300.timing hyper512 color2048 --backward --bruteforce
 """
 from __future__ import annotations
 
@@ -37,7 +37,7 @@ def median_ms(fn, reps: int = 10) -> float:
     return float(np.median(ts))
 
 
-def workload_times(name: str, backward: bool = False) -> dict:
+def workload_times(name: str, backward: bool = False, bruteforce: bool = False) -> dict:
     w = synthetic.workload(name)
     f = torch.from_numpy(w["f"]).cuda()
     n, H, W = f.shape
@@ -65,6 +65,10 @@ def workload_times(name: str, backward: bool = False) -> dict:
                                 generator=torch.Generator(device=f.device).manual_seed(5))
                 out["backward_ms"] = median_ms(lambda: flt.backward(f, p, G))
             out[f"stats_{spatial}"] = flt.stats()
+            if bruteforce and spatial == "gauss":   # Eq. (1)-(2) on the same guide
+                gb = api.bruteforce(f, p, w["sigma_s"], w["sigma_r"])
+                out["bruteforce_ms"] = median_ms(
+                    lambda: api.bruteforce(f, p, w["sigma_s"], w["sigma_r"], out=gb), reps=3)
         finally:
             flt.close()
     return out
@@ -75,6 +79,8 @@ def parse_args(argv=None) -> argparse.Namespace:
     ap.add_argument("workloads", nargs="*", metavar="workload",
                     help=f"one or more of {', '.join(WORKLOADS)} (default: all)")
     ap.add_argument("--backward", action="store_true", help="also time the gradient pass")
+    ap.add_argument("--bruteforce", action="store_true",
+                    help="also time the brute-force filter (Eq. (1)-(2))")
     args = ap.parse_args(argv)
     bad = [w for w in args.workloads if w not in WORKLOADS]
     if bad:
@@ -86,7 +92,7 @@ def parse_args(argv=None) -> argparse.Namespace:
 def main() -> None:
     args = parse_args()
     for name in args.workloads:
-        print(json.dumps(workload_times(name, args.backward)), flush=True)
+        print(json.dumps(workload_times(name, args.backward, args.bruteforce)), flush=True)
 
 
 if __name__ == "__main__":

@@ -111,3 +111,28 @@ def test_backward_word_and_vector_staging_agree(api, ss):
     gm, sm, rm = flt.backward(fm, fm, G)
     assert torch.equal(ga, gm)
     assert float(sa) == float(sm) and float(ra) == float(rm)
+
+
+def test_backward_equals_brute_force_gradients_at_exactness(api):
+    """With a separate guide of 4 distinct values and one centre per value,
+    Algorithm 1 equals the brute force for every f, sigma_s and sigma_r, so
+    the device's backward pass must give the gradients of the brute force
+    (FP64 autograd through Eq. (1)-(2))."""
+    rng = np.random.default_rng(86)
+    vals = rng.uniform(0, 1, size=(4, 2)).astype(np.float32)
+    p = np.ascontiguousarray(np.moveaxis(vals[rng.integers(0, 4, size=(40, 37))], -1, 0))
+    f = rng.uniform(0, 1, size=(3, 40, 37)).astype(np.float32)
+    G = rng.normal(size=f.shape).astype(np.float32)
+    ss, sr = 1.5, 0.3
+    S = O.window_halfwidth(ss)
+    bf, bls, blr, _ = OG.brute_grads(f.astype(np.float64), p.astype(np.float64), ss, sr, S,
+                                     G.astype(np.float64))
+    flt = api.HDFilter(40, 37, 3, 2, 4, ss, sr)
+    flt.set_centers(vals)
+    gf, gls, glr = flt.backward(torch.from_numpy(f).cuda(), torch.from_numpy(p).cuda(),
+                                torch.from_numpy(G).cuda())
+    gf = gf.cpu().numpy()
+    scale = np.abs(bf).max()
+    assert np.max(np.abs(gf - bf)) <= RTOL * scale
+    assert abs(float(gls) - bls) <= RTOL * max(abs(bls), 1e-3 * scale)
+    assert abs(float(glr) - blr) <= RTOL * max(abs(blr), 1e-3 * scale)

@@ -6,9 +6,9 @@
 //
 // Kernels: per-channel means (shift against cancellation), per-block sums of
 // shifted patch vectors and their products (FP32 within a block, FP64 across
-// blocks), one CTA for the FP64 covariance and its eigendecomposition (cyclic
-// Jacobi in round-robin order: D/2 disjoint rotations per step), and the
-// projection.
+// blocks), one CTA for the covariance and its eigendecomposition (cyclic
+// Jacobi in round-robin order, D/2 disjoint rotations per step, in float32),
+// and the projection.
 #include <math.h>
 
 #include "hdf_internal.cuh"
@@ -61,7 +61,8 @@ nlm_cov_kernel(const float* __restrict__ f, int n, int H, int W, int m, const do
   extern __shared__ float sm[];
   const int D = n * m * m;
   const int NP = D * (D + 1) / 2;
-  float* sX = sm;                                   // [D][NL_TILE*NL_TILE] shifted patch values
+  const int LDX = D | 1;                            // odd pitch: a warp's reads hit distinct banks
+  float* sX = sm;                                   // [NL_TILE*NL_TILE][LDX] shifted patch values
   __shared__ float shift[4];
   if (threadIdx.x < n) {
     double t = 0.0;
@@ -90,17 +91,17 @@ nlm_cov_kernel(const float* __restrict__ f, int n, int H, int W, int m, const do
       const int y = y0 + pix / NL_TILE, x = x0 + pix % NL_TILE;
       float v = 0.0f;
       if (y < H && x < W) v = patch_val(f, H, W, m, a, y, x) - shift[a / (m * m)];
-      sX[a * NL_TILE * NL_TILE + pix] = v;          // 0 outside the image: contributes nothing
+      sX[pix * LDX + a] = v;                        // 0 outside the image: contributes nothing
     }
     __syncthreads();
     for (int pix = 0; pix < NL_TILE * NL_TILE; ++pix) {
+      const float* xr = sX + pix * LDX;
 #pragma unroll
       for (int j = 0; j < PER; ++j)
-        if (pa[j] >= 0)
-          acc[j] = fmaf(sX[pa[j] * NL_TILE * NL_TILE + pix], sX[pb[j] * NL_TILE * NL_TILE + pix], acc[j]);
+        if (pa[j] >= 0) acc[j] = fmaf(xr[pa[j]], xr[pb[j]], acc[j]);
     }
     if ((int)threadIdx.x < D)
-      for (int pix = 0; pix < NL_TILE * NL_TILE; ++pix) acc1 += sX[threadIdx.x * NL_TILE * NL_TILE + pix];
+      for (int pix = 0; pix < NL_TILE * NL_TILE; ++pix) acc1 += sX[pix * LDX + threadIdx.x];
   }
   float* out = part + (size_t)blockIdx.x * (NP + D);
 #pragma unroll
@@ -109,7 +110,14 @@ nlm_cov_kernel(const float* __restrict__ f, int n, int H, int W, int m, const do
   if ((int)threadIdx.x < D) out[NP + threadIdx.x] = acc1;
 }
 
-// One CTA: covariance in FP64, Jacobi eigendecomposition, top-rho basis.
+// One CTA: the covariance in FP64 (sums of the blocks' float32 partials), its
+// eigendecomposition by cyclic Jacobi in float32, the top-rho basis.  The
+// blocks' partial sums are float32 sums over some 7000 pixels each, so the
+// covariance carries a relative rounding of order 1e-6; float32 rotations
+// (1e-7) add nothing of consequence, and on this GPU they run at the FP32
+// rate instead of the much lower FP64 one.  Threshold rule: a pair (p, q) is
+// rotated only while |a_pq| exceeds 2^-23 sqrt(|a_pp a_qq|) (below that the
+// rotation is a no-op in float32); the sweeps stop after one without rotations.
 __global__ void __launch_bounds__(NL_THREADS)
 nlm_eig_kernel(const float* __restrict__ part, int nblk, int n, int m, int N, int rho,
                const double* mean_part, int nblk_mean, float* __restrict__ basis,
@@ -117,13 +125,13 @@ nlm_eig_kernel(const float* __restrict__ part, int nblk, int n, int m, int N, in
   extern __shared__ double dm[];
   const int D = n * m * m, NP = D * (D + 1) / 2;
   const int DE = D + (D & 1);                       // even size for the round-robin schedule
-  double* A = dm;                                   // DE x DE
-  double* V = A + DE * DE;                          // DE x DE eigenvectors (columns)
-  double* mu = V + DE * DE;                         // D  mean of the shifted patch vectors
-  __shared__ double cs[NL_MAXD / 2 + 1][2];
+  double* mu = dm;                                  // D  mean of the shifted patch vectors
+  float* A = (float*)(mu + D + (D & 1));            // DE x DE
+  float* V = A + DE * DE;                           // DE x DE eigenvectors (columns)
+  __shared__ float cs[NL_MAXD / 2 + 1][2];
   __shared__ int pp[NL_MAXD / 2 + 1], qq[NL_MAXD / 2 + 1];
-  __shared__ double red[NL_THREADS];
   __shared__ double shift[4];
+  __shared__ int rotated;
   const int tid = threadIdx.x;
   if (tid < n) {
     double t = 0.0;
@@ -146,34 +154,14 @@ nlm_eig_kernel(const float* __restrict__ part, int nblk, int n, int m, int N, in
       for (int bl = 0; bl < nblk; ++bl) t += (double)part[(size_t)bl * (NP + D) + q];
       v = t / (double)N - mu[a] * mu[b];
     }
-    A[idx] = v;
-    V[idx] = (i == j) ? 1.0 : 0.0;
+    A[idx] = (float)v;
+    V[idx] = (i == j) ? 1.0f : 0.0f;
   }
   __syncthreads();
   const int half = DE / 2;
   for (int sweep = 0; sweep < 40; ++sweep) {
-    double off = 0.0, dia = 0.0;
-    for (int idx = tid; idx < DE * DE; idx += NL_THREADS) {
-      const double v = A[idx] * A[idx];
-      if (idx / DE == idx % DE) dia += v; else off += v;
-    }
-    red[tid] = off;
+    if (tid == 0) rotated = 0;
     __syncthreads();
-    for (int o = NL_THREADS / 2; o > 0; o >>= 1) {
-      if (tid < o) red[tid] += red[tid + o];
-      __syncthreads();
-    }
-    const double off_all = red[0];
-    __syncthreads();
-    red[tid] = dia;
-    __syncthreads();
-    for (int o = NL_THREADS / 2; o > 0; o >>= 1) {
-      if (tid < o) red[tid] += red[tid + o];
-      __syncthreads();
-    }
-    const double dia_all = red[0];
-    __syncthreads();
-    if (off_all <= 1e-30 * dia_all || off_all == 0.0) break;
     for (int r = 0; r < DE - 1; ++r) {
       if (tid < half) {   // round-robin pairs: position 0 fixed, the others rotate
         const int j = tid;
@@ -182,41 +170,48 @@ nlm_eig_kernel(const float* __restrict__ part, int nblk, int n, int m, int N, in
         if (p > q) { const int t = p; p = q; q = t; }
         pp[j] = p;
         qq[j] = q;
-        double c = 1.0, s = 0.0;
-        const double apq = A[p * DE + q];
-        if (apq != 0.0) {
-          const double tau = (A[q * DE + q] - A[p * DE + p]) / (2.0 * apq);
-          const double t = tau >= 0.0 ? 1.0 / (tau + sqrt(1.0 + tau * tau))
-                                      : -1.0 / (-tau + sqrt(1.0 + tau * tau));
-          c = 1.0 / sqrt(1.0 + t * t);
-          s = t * c;
+        float c = 1.0f, sn = 0.0f;
+        const float apq = A[p * DE + q];
+        const float app = A[p * DE + p], aqq = A[q * DE + q];
+        if (fabsf(apq) > 1.1920929e-7f * sqrtf(fabsf(app * aqq)) && apq != 0.0f) {
+          const float tau = (aqq - app) / (2.0f * apq);
+          const float t = tau >= 0.0f ? 1.0f / (tau + sqrtf(1.0f + tau * tau))
+                                      : -1.0f / (-tau + sqrtf(1.0f + tau * tau));
+          c = 1.0f / sqrtf(1.0f + t * t);
+          sn = t * c;
+          rotated = 1;
         }
         cs[j][0] = c;
-        cs[j][1] = s;
+        cs[j][1] = sn;
       }
       __syncthreads();
       for (int idx = tid; idx < DE * half; idx += NL_THREADS) {   // columns p, q of A J and V J
         const int k = idx / half, j = idx % half;
+        const float c = cs[j][0], sn = cs[j][1];
+        if (sn == 0.0f) continue;
         const int p = pp[j], q = qq[j];
-        const double c = cs[j][0], s = cs[j][1];
-        const double ap = A[k * DE + p], aq = A[k * DE + q];
-        A[k * DE + p] = c * ap - s * aq;
-        A[k * DE + q] = s * ap + c * aq;
-        const double vp = V[k * DE + p], vq = V[k * DE + q];
-        V[k * DE + p] = c * vp - s * vq;
-        V[k * DE + q] = s * vp + c * vq;
+        const float ap = A[k * DE + p], aq = A[k * DE + q];
+        A[k * DE + p] = c * ap - sn * aq;
+        A[k * DE + q] = sn * ap + c * aq;
+        const float vp = V[k * DE + p], vq = V[k * DE + q];
+        V[k * DE + p] = c * vp - sn * vq;
+        V[k * DE + q] = sn * vp + c * vq;
       }
       __syncthreads();
       for (int idx = tid; idx < DE * half; idx += NL_THREADS) {   // rows p, q of J^T (A J)
         const int j = idx / DE, k = idx % DE;
+        const float c = cs[j][0], sn = cs[j][1];
+        if (sn == 0.0f) continue;
         const int p = pp[j], q = qq[j];
-        const double c = cs[j][0], s = cs[j][1];
-        const double ap = A[p * DE + k], aq = A[q * DE + k];
-        A[p * DE + k] = c * ap - s * aq;
-        A[q * DE + k] = s * ap + c * aq;
+        const float ap = A[p * DE + k], aq = A[q * DE + k];
+        A[p * DE + k] = c * ap - sn * aq;
+        A[q * DE + k] = sn * ap + c * aq;
       }
       __syncthreads();
     }
+    const int any = rotated;   // read after the barrier that ended the sweep's last step
+    __syncthreads();           // everyone has read it before thread 0 resets it
+    if (!any) break;
   }
   // the rho largest eigenvalues (ties -> lower index); basis[d][a], mean patch
   if (tid == 0) {
@@ -233,7 +228,7 @@ nlm_eig_kernel(const float* __restrict__ part, int nblk, int n, int m, int N, in
   __syncthreads();
   for (int idx = tid; idx < rho * D; idx += NL_THREADS) {
     const int d = idx / D, a = idx % D;
-    basis[idx] = (float)V[a * DE + pp[d]];
+    basis[idx] = V[a * DE + pp[d]];
   }
   for (int a = tid; a < D; a += NL_THREADS) pmean[a] = (float)(mu[a] + shift[a / (m * m)]);
   (void)ctrl;
@@ -297,7 +292,7 @@ cudaError_t launch_nlm_guide(const float* f, int n, int H, int W, int m, int rho
   float* pmean = basis + rho * D;
   const int N = H * W;
   nlm_mean_kernel<<<G, NL_THREADS, 0, st>>>(f, n, N, mean_part);
-  const size_t smem_cov = sizeof(float) * (size_t)D * NL_TILE * NL_TILE;
+  const size_t smem_cov = sizeof(float) * (size_t)(D | 1) * NL_TILE * NL_TILE;
   cudaError_t e;
   if (NP <= 8 * NL_THREADS) {
     e = cudaFuncSetAttribute(nlm_cov_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cov);
@@ -309,7 +304,7 @@ cudaError_t launch_nlm_guide(const float* f, int n, int H, int W, int m, int rho
     nlm_cov_kernel<24><<<G, NL_THREADS, smem_cov, st>>>(f, n, H, W, m, mean_part, G, cov_part);
   }
   const int DE = D + (D & 1);
-  const size_t smem_eig = sizeof(double) * (2 * (size_t)DE * DE + D);
+  const size_t smem_eig = sizeof(double) * (size_t)(D + (D & 1)) + sizeof(float) * 2 * (size_t)DE * DE;
   e = cudaFuncSetAttribute(nlm_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_eig);
   if (e != cudaSuccess) return e;
   nlm_eig_kernel<<<1, NL_THREADS, smem_eig, st>>>(cov_part, G, n, m, N, rho, mean_part, G, basis,

@@ -24,6 +24,31 @@ namespace {
 constexpr int RS_THREADS = 128;
 constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_CB = 8;   // channels summed together
+constexpr int EXP_INT = 746;   // exp(-a), a = 0 .. 745 (beyond, exp(-x) underflows to 0)
+constexpr int EXP_FRAC = 64;   // exp(-b / 64), b = 0 .. 63
+
+// exp(-x) for x >= 0 in FP64 from two tables and a short polynomial:
+// x = a + b / 64 + r with integers a, b and 0 <= r < 1/64, so that
+// exp(-x) = exp(-a) exp(-b / 64) exp(-r), the last by its Taylor polynomial
+// of degree 7 (truncation below (1/64)^8 / 8! < 2e-19).  The tables hold
+// values of CUDA's exp computed once per block; the products carry a few
+// units of 2^-53.  About half the FP64 operations of a general exp.
+__device__ __forceinline__ double exp_neg(double x, const double* e_int, const double* e_frac) {
+  if (!(x < (double)EXP_INT)) return 0.0;
+  const double x64 = x * 64.0;
+  const int k = (int)x64;                 // floor for x >= 0
+  const int a = k >> 6, b = k & 63;
+  const double r = (x64 - (double)k) * (1.0 / 64.0);   // exact: x64 - k < 1, then a power of 2
+  double q = -1.0 / 5040.0;               // Horner for sum_{i<=7} (-r)^i / i!
+  q = fma(q, r, 1.0 / 720.0);
+  q = fma(q, r, -1.0 / 120.0);
+  q = fma(q, r, 1.0 / 24.0);
+  q = fma(q, r, -1.0 / 6.0);
+  q = fma(q, r, 0.5);
+  q = fma(q, r, -1.0);
+  q = fma(q, r, 1.0);
+  return e_int[a] * e_frac[b] * q;
+}
 
 struct RescueArgs {
   const float* f;        // (n, H, W)
@@ -80,6 +105,7 @@ rescue_kernel(const RescueArgs a) {
   __shared__ double s_sum[HDF_MAX_K + 1];
   __shared__ int s_s, s_guard;
   __shared__ double s_den, s_rs;
+  __shared__ double e_int[EXP_INT], e_frac[EXP_FRAC];
   const int tid = threadIdx.x;
   int count = a.ctrl[CTRL_RESCUED];
   if (count > (int)N) count = (int)N;
@@ -89,6 +115,8 @@ rescue_kernel(const RescueArgs a) {
     s_w1[t] = a.box ? 1.0 : exp(-(j * j) / (2.0 * a.sigma_s * a.sigma_s));
   }
   for (int i = tid; i < K * rho; i += RS_THREADS) smu[i] = (double)a.mu[i];
+  for (int i = tid; i < EXP_INT; i += RS_THREADS) e_int[i] = exp(-(double)i);
+  for (int i = tid; i < EXP_FRAC; i += RS_THREADS) e_frac[i] = exp(-(double)i / 64.0);
   for (int e = blockIdx.x; e < count; e += gridDim.x) {
     const int pix = a.list[N - 1 - e];
     if (pix < 0 || (size_t)pix >= N) {   // inconsistent list: record, write nothing
@@ -106,7 +134,7 @@ rescue_kernel(const RescueArgs a) {
         d2 = fma(t, t, d2);
       }
       s_d2[k] = d2;
-      s_b[k] = exp(-d2 * a.inv2sr2);
+      s_b[k] = exp_neg(d2 * a.inv2sr2, e_int, e_frac);
     }
     __syncthreads();
     if (tid == 0) {   // nearest centre, ties -> lowest k
@@ -146,7 +174,7 @@ rescue_kernel(const RescueArgs a) {
             const double t = xq[d] - smu[k * rho + d];
             d2 = fma(t, t, d2);
           }
-          const double ph = exp(-d2 * a.inv2sr2);
+          const double ph = exp_neg(d2 * a.inv2sr2, e_int, e_frac);
           part[k] = fma(wt, ph, part[k]);
           beta = fma(s_c[k], ph, beta);
           if (k == s) phs = ph;

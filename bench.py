@@ -389,6 +389,9 @@ def measure_batch(reps: int, stream, flush, dev) -> dict:
     px = sum(s["H"] * s["W"] for s in specs)
     b = api.Batch(specs)
     b.bind(fs, gs)
+    t0 = time.perf_counter()
+    trials = b.tune(reps=2)           # clustering plan and tile shapes (hdf_batch_tune)
+    tune_s = time.perf_counter() - t0
     for _ in range(2):
         b.run(graph=True)
     ms = statistics.median(_timed(lambda: b.run(graph=True), reps, stream, flush))
@@ -397,9 +400,11 @@ def measure_batch(reps: int, stream, flush, dev) -> dict:
     names = ["reset", "bf16_guides", "clustering", "fit", "range_maps", "tiles", "normalise"]
     info = b.info()
     b.close()
+    chosen = [{k: tr[k] for k in ("SB", "planes", "P", "TY", "ms")} for tr in trials if tr["chosen"]]
     return {"images": len(specs), "megapixels": px / 1e6, "run_ms": ms,
             "mps": px / (ms * 1e-3) / 1e6, "stage_ms": dict(zip(names, t)),
-            "launches_per_run": info["launches_per_run"], "graph_state": info["graph_state"]}
+            "launches_per_run": info["launches_per_run"], "graph_state": info["graph_state"],
+            "clustering_groups": info["ngroups"], "tuned": chosen, "tune_s": tune_s}
 
 
 def run_gpu(args) -> None:

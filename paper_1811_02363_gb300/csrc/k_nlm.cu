@@ -117,7 +117,10 @@ nlm_cov_kernel(const float* __restrict__ f, int n, int H, int W, int m, const do
 // (1e-7) add nothing of consequence, and on this GPU they run at the FP32
 // rate instead of the much lower FP64 one.  Threshold rule: a pair (p, q) is
 // rotated only while |a_pq| exceeds 2^-23 sqrt(|a_pp a_qq|) (below that the
-// rotation is a no-op in float32); the sweeps stop after one without rotations.
+// rotation is a no-op in float32); the sweeps stop after one without
+// rotations, at the float32 rounding level of the off-diagonal norm, or when
+// a sweep no longer halves that norm (Jacobi converges quadratically until
+// rounding noise is all that is left).
 __global__ void __launch_bounds__(NL_THREADS)
 nlm_eig_kernel(const float* __restrict__ part, int nblk, int n, int m, int N, int rho,
                const double* mean_part, int nblk_mean, float* __restrict__ basis,
@@ -159,8 +162,37 @@ nlm_eig_kernel(const float* __restrict__ part, int nblk, int n, int m, int N, in
   }
   __syncthreads();
   const int half = DE / 2;
+  __shared__ float red[NL_THREADS];
+  __shared__ float off_prev;
   for (int sweep = 0; sweep < 40; ++sweep) {
-    if (tid == 0) rotated = 0;
+    // off-diagonal and diagonal squared norms: stop at float32 rounding level
+    // (off <= 2^-23 dia), or once a sweep no longer halves off (stagnation:
+    // the rotations would only move rounding noise around)
+    float off = 0.0f, dia = 0.0f;
+    for (int idx = tid; idx < DE * DE; idx += NL_THREADS) {
+      const float v = A[idx] * A[idx];
+      if (idx / DE == idx % DE) dia += v; else off += v;
+    }
+    red[tid] = off;
+    __syncthreads();
+    for (int o = NL_THREADS / 2; o > 0; o >>= 1) {
+      if (tid < o) red[tid] += red[tid + o];
+      __syncthreads();
+    }
+    const float off_all = red[0];
+    __syncthreads();
+    red[tid] = dia;
+    __syncthreads();
+    for (int o = NL_THREADS / 2; o > 0; o >>= 1) {
+      if (tid < o) red[tid] += red[tid + o];
+      __syncthreads();
+    }
+    const float dia_all = red[0];
+    const bool stop = off_all <= 1.42e-14f * dia_all ||          // (2^-23)^2
+                      (sweep >= 3 && off_all > 0.25f * off_prev);  // norm not halved
+    __syncthreads();
+    if (tid == 0) { off_prev = off_all; rotated = 0; }
+    if (stop) break;
     __syncthreads();
     for (int r = 0; r < DE - 1; ++r) {
       if (tid < half) {   // round-robin pairs: position 0 fixed, the others rotate

@@ -223,7 +223,7 @@ cudaError_t launch_backward(hdf_handle* h, const float* f, const void* p, const 
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaError_t e;
-  const int ty = SB > 18 ? 32 : 64;            // tile height of the backward tile kernels
+  const int ty = SB > 24 ? 32 : 64;            // tile height of the backward tile kernels
   const int ntiles = ((d.W + 31) / 32) * ((d.H + ty - 1) / ty);
   if (ntiles > PART_SIGMA_R) return cudaErrorInvalidValue;   // per-tile partials must fit
   // 1. forward recompute (g_hat into scratch, D, guard list)

@@ -1,5 +1,6 @@
-// Backward tile kernels for window half-widths 15, 18, 24, 32 (tile height 32
-// beyond 18 so that the two row-pass outputs fit in shared memory).
+// Backward tile kernels for window half-widths 15, 18, 24, 32 (tile height 64;
+// 32 for the widest bucket, where the two row-pass outputs of a 64-row tile
+// would not fit in shared memory).
 #include "bwd_tile.cuh"
 
 namespace hdf {
@@ -13,14 +14,14 @@ cudaError_t launch_bwd_sb(int SB, int mode, const BwdArgs& a, const Taps& t1, co
     switch (SB) {
       case 15: return launch_bwd_tile<15, MODE_GAMMA, 64>(a, t1, t2, st);
       case 18: return launch_bwd_tile<18, MODE_GAMMA, 64>(a, t1, t2, st);
-      case 24: return launch_bwd_tile<24, MODE_GAMMA, 32>(a, t1, t2, st);
+      case 24: return launch_bwd_tile<24, MODE_GAMMA, 64>(a, t1, t2, st);
       case 32: return launch_bwd_tile<32, MODE_GAMMA, 32>(a, t1, t2, st);
     }
   } else {
     switch (SB) {
       case 15: return launch_bwd_tile<15, MODE_ADJ, 64>(a, t1, t2, st);
       case 18: return launch_bwd_tile<18, MODE_ADJ, 64>(a, t1, t2, st);
-      case 24: return launch_bwd_tile<24, MODE_ADJ, 32>(a, t1, t2, st);
+      case 24: return launch_bwd_tile<24, MODE_ADJ, 64>(a, t1, t2, st);
       case 32: return launch_bwd_tile<32, MODE_ADJ, 32>(a, t1, t2, st);
     }
   }

@@ -52,62 +52,103 @@ __global__ void nlm_mean_kernel(const float* __restrict__ f, int n, int N, doubl
   }
 }
 
-// Per block: sum of (X - s) and of (X - s)(X - s)^T (upper triangle) over the
-// block's tiles, s = per-channel mean.
-template <int PER>
+// Per-block sums of the shifted patch vectors and of their pairwise products
+// over the block's tiles of NL_TILE x NL_TILE pixels (s = per-channel mean):
+// part[blk] = [sum_i (x_a - s)(x_b - s) for a <= b in row-major pair order,
+// then sum_i (x_a - s)].  The patch values of a tile are staged pixel-major
+// (odd pitch); each thread accumulates a 4 x 4 block of the covariance over
+// one parity class of the tile's pixels (8 shared loads per 16 FMAs), and the
+// parity classes are added in a fixed order at the end.
 __global__ void __launch_bounds__(NL_THREADS)
 nlm_cov_kernel(const float* __restrict__ f, int n, int H, int W, int m, const double* mean_part,
                int nblk_mean, float* __restrict__ part) {
   extern __shared__ float sm[];
   const int D = n * m * m;
   const int NP = D * (D + 1) / 2;
-  const int LDX = D | 1;                            // odd pitch: a warp's reads hit distinct banks
+  const int DP = (D + 3) & ~3;                      // padded to whole 4 x 4 blocks (zeros)
+  const int LDX = DP | 1;                           // odd pitch: a warp's reads hit distinct banks
+  const int NBR = DP / 4;                           // block rows
+  const int NB = NBR * (NBR + 1) / 2;               // blocks bi <= bj
+  const int NPAR = NB <= NL_THREADS ? NL_THREADS / NB : 1;   // pixel parity classes
   float* sX = sm;                                   // [NL_TILE*NL_TILE][LDX] shifted patch values
+  float* sAcc = sm + NL_TILE * NL_TILE * LDX;       // [NPAR][NB][16] the classes' block sums
   __shared__ float shift[4];
-  if (threadIdx.x < n) {
+  const int tid = threadIdx.x;
+  if (tid < n) {
     double t = 0.0;
-    for (int b = 0; b < nblk_mean; ++b) t += mean_part[(size_t)b * n + threadIdx.x];
-    shift[threadIdx.x] = (float)(t / ((double)H * W));
+    for (int b = 0; b < nblk_mean; ++b) t += mean_part[(size_t)b * n + tid];
+    shift[tid] = (float)(t / ((double)H * W));
   }
   __syncthreads();
-  float acc[PER], acc1 = 0.0f;
-#pragma unroll
-  for (int j = 0; j < PER; ++j) acc[j] = 0.0f;
-  int pa[PER], pb[PER];
-#pragma unroll
-  for (int j = 0; j < PER; ++j) {
-    int q = threadIdx.x + j * NL_THREADS, a = 0;
-    if (q >= NP) { pa[j] = -1; pb[j] = -1; continue; }
-    while (q >= D - a) { q -= D - a; ++a; }         // q-th pair of row a: (a, a + q)
-    pa[j] = a;
-    pb[j] = a + q;
-  }
+  const int first = NB <= NL_THREADS ? tid % NB : tid;   // this thread's first block
+  const int par = NB <= NL_THREADS ? tid / NB : 0;       // and its pixel class
+  float acc1 = 0.0f;
   const int tiles_x = (W + NL_TILE - 1) / NL_TILE, tiles = tiles_x * ((H + NL_TILE - 1) / NL_TILE);
-  for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
-    const int y0 = (t / tiles_x) * NL_TILE, x0 = (t % tiles_x) * NL_TILE;
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < D * NL_TILE * NL_TILE; idx += NL_THREADS) {
-      const int a = idx / (NL_TILE * NL_TILE), pix = idx % (NL_TILE * NL_TILE);
-      const int y = y0 + pix / NL_TILE, x = x0 + pix % NL_TILE;
-      float v = 0.0f;
-      if (y < H && x < W) v = patch_val(f, H, W, m, a, y, x) - shift[a / (m * m)];
-      sX[pix * LDX + a] = v;                        // 0 outside the image: contributes nothing
-    }
-    __syncthreads();
-    for (int pix = 0; pix < NL_TILE * NL_TILE; ++pix) {
-      const float* xr = sX + pix * LDX;
+  // blocks b = first, first + 256, ... (a single one while NB <= 256); every
+  // thread runs the same number of block passes so that the barriers match
+  const int npass = (NB + NL_THREADS - 1) / NL_THREADS;
+  for (int ps = 0; ps < npass; ++ps) {
+    const int b0 = first + ps * NL_THREADS;
+    const bool active = par < NPAR && b0 < NB;
+    int bi = 0, rem = active ? b0 : 0;              // b0 -> (bi, bj), bi <= bj, row-major
+    while (rem >= NBR - bi) { rem -= NBR - bi; ++bi; }
+    const int bj = bi + rem;
+    float acc[4][4];
 #pragma unroll
-      for (int j = 0; j < PER; ++j)
-        if (pa[j] >= 0) acc[j] = fmaf(xr[pa[j]], xr[pb[j]], acc[j]);
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[r][c] = 0.0f;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+      const int y0 = (t / tiles_x) * NL_TILE, x0 = (t % tiles_x) * NL_TILE;
+      __syncthreads();
+      for (int idx = tid; idx < DP * NL_TILE * NL_TILE; idx += NL_THREADS) {
+        const int a = idx / (NL_TILE * NL_TILE), pix = idx % (NL_TILE * NL_TILE);
+        const int y = y0 + pix / NL_TILE, x = x0 + pix % NL_TILE;
+        float v = 0.0f;
+        if (a < D && y < H && x < W) v = patch_val(f, H, W, m, a, y, x) - shift[a / (m * m)];
+        sX[pix * LDX + a] = v;                      // 0 outside the image and beyond D
+      }
+      __syncthreads();
+      if (active) {
+        for (int pix = par; pix < NL_TILE * NL_TILE; pix += NPAR) {
+          const float* xr = sX + pix * LDX;
+          float xa[4], xb[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            xa[r] = xr[4 * bi + r];
+            xb[r] = xr[4 * bj + r];
+          }
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(xa[r], xb[c], acc[r][c]);
+        }
+      }
+      if (ps == 0 && tid < D)
+        for (int pix = 0; pix < NL_TILE * NL_TILE; ++pix) acc1 += sX[pix * LDX + tid];
     }
-    if ((int)threadIdx.x < D)
-      for (int pix = 0; pix < NL_TILE * NL_TILE; ++pix) acc1 += sX[pix * LDX + threadIdx.x];
+    if (active) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) sAcc[((size_t)par * NB + b0) * 16 + 4 * r + c] = acc[r][c];
+    }
   }
+  __syncthreads();
+  // combine the parity classes in order and write the upper triangle
   float* out = part + (size_t)blockIdx.x * (NP + D);
-#pragma unroll
-  for (int j = 0; j < PER; ++j)
-    if (pa[j] >= 0) out[threadIdx.x + j * NL_THREADS] = acc[j];
-  if ((int)threadIdx.x < D) out[NP + threadIdx.x] = acc1;
+  for (int v = tid; v < NB * 16; v += NL_THREADS) {
+    const int b0 = v / 16, rc = v % 16, r = rc / 4, c = rc % 4;
+    int bi = 0, rem = b0;
+    while (rem >= NBR - bi) { rem -= NBR - bi; ++bi; }
+    const int bj = bi + rem;
+    const int a = 4 * bi + r, bb = 4 * bj + c;
+    if (a >= D || bb >= D || a > bb) continue;
+    float t = sAcc[(size_t)b0 * 16 + rc];
+    for (int q = 1; q < NPAR; ++q) t += sAcc[((size_t)q * NB + b0) * 16 + rc];
+    out[a * D - a * (a - 1) / 2 + (bb - a)] = t;
+  }
+  if (tid < D) out[NP + tid] = acc1;
 }
 
 // One CTA: the covariance in FP64 (sums of the blocks' float32 partials), its
@@ -217,27 +258,32 @@ nlm_eig_kernel(const float* __restrict__ part, int nblk, int n, int m, int N, in
         cs[j][1] = sn;
       }
       __syncthreads();
-      for (int idx = tid; idx < DE * half; idx += NL_THREADS) {   // columns p, q of A J and V J
-        const int k = idx / half, j = idx % half;
+      // a lane per rotation (pair j), the block's warps over the rows k
+      constexpr int NG = NL_THREADS / 32;
+      const int lane = tid & 31, grp = tid >> 5;
+      for (int j = lane; j < half; j += 32) {   // columns p, q of A J and V J
         const float c = cs[j][0], sn = cs[j][1];
         if (sn == 0.0f) continue;
         const int p = pp[j], q = qq[j];
-        const float ap = A[k * DE + p], aq = A[k * DE + q];
-        A[k * DE + p] = c * ap - sn * aq;
-        A[k * DE + q] = sn * ap + c * aq;
-        const float vp = V[k * DE + p], vq = V[k * DE + q];
-        V[k * DE + p] = c * vp - sn * vq;
-        V[k * DE + q] = sn * vp + c * vq;
+        for (int k = grp; k < DE; k += NG) {
+          const float ap = A[k * DE + p], aq = A[k * DE + q];
+          A[k * DE + p] = c * ap - sn * aq;
+          A[k * DE + q] = sn * ap + c * aq;
+          const float vp = V[k * DE + p], vq = V[k * DE + q];
+          V[k * DE + p] = c * vp - sn * vq;
+          V[k * DE + q] = sn * vp + c * vq;
+        }
       }
       __syncthreads();
-      for (int idx = tid; idx < DE * half; idx += NL_THREADS) {   // rows p, q of J^T (A J)
-        const int j = idx / DE, k = idx % DE;
+      for (int j = lane; j < half; j += 32) {   // rows p, q of J^T (A J)
         const float c = cs[j][0], sn = cs[j][1];
         if (sn == 0.0f) continue;
         const int p = pp[j], q = qq[j];
-        const float ap = A[p * DE + k], aq = A[q * DE + k];
-        A[p * DE + k] = c * ap - sn * aq;
-        A[q * DE + k] = sn * ap + c * aq;
+        for (int k = grp; k < DE; k += NG) {
+          const float ap = A[p * DE + k], aq = A[q * DE + k];
+          A[p * DE + k] = c * ap - sn * aq;
+          A[q * DE + k] = sn * ap + c * aq;
+        }
       }
       __syncthreads();
     }
@@ -311,7 +357,6 @@ cudaError_t launch_nlm_guide(const float* f, int n, int H, int W, int m, int rho
       W < m / 2 + 1)
     return cudaErrorInvalidValue;
   const int NP = D * (D + 1) / 2;
-  if (NP > 24 * NL_THREADS) return cudaErrorInvalidValue;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -324,17 +369,14 @@ cudaError_t launch_nlm_guide(const float* f, int n, int H, int W, int m, int rho
   float* pmean = basis + rho * D;
   const int N = H * W;
   nlm_mean_kernel<<<G, NL_THREADS, 0, st>>>(f, n, N, mean_part);
-  const size_t smem_cov = sizeof(float) * (size_t)(D | 1) * NL_TILE * NL_TILE;
-  cudaError_t e;
-  if (NP <= 8 * NL_THREADS) {
-    e = cudaFuncSetAttribute(nlm_cov_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cov);
-    if (e != cudaSuccess) return e;
-    nlm_cov_kernel<8><<<G, NL_THREADS, smem_cov, st>>>(f, n, H, W, m, mean_part, G, cov_part);
-  } else {
-    e = cudaFuncSetAttribute(nlm_cov_kernel<24>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cov);
-    if (e != cudaSuccess) return e;
-    nlm_cov_kernel<24><<<G, NL_THREADS, smem_cov, st>>>(f, n, H, W, m, mean_part, G, cov_part);
-  }
+  const int DP = (D + 3) & ~3, NBR = DP / 4, NB = NBR * (NBR + 1) / 2;
+  const int NPAR = NB <= NL_THREADS ? NL_THREADS / NB : 1;
+  const size_t smem_cov =
+      sizeof(float) * ((size_t)(DP | 1) * NL_TILE * NL_TILE + (size_t)NPAR * NB * 16);
+  cudaError_t e = cudaFuncSetAttribute(nlm_cov_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_cov);
+  if (e != cudaSuccess) return e;
+  nlm_cov_kernel<<<G, NL_THREADS, smem_cov, st>>>(f, n, H, W, m, mean_part, G, cov_part);
   const int DE = D + (D & 1);
   const size_t smem_eig = sizeof(double) * (size_t)(D + (D & 1)) + sizeof(float) * 2 * (size_t)DE * DE;
   e = cudaFuncSetAttribute(nlm_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_eig);

@@ -154,6 +154,21 @@ hdf_status hdf_cluster(hdf_handle* h, const void* d_p, void* stream);
  * until the stream reaches it; pageable memory makes it synchronous). */
 hdf_status hdf_set_centers(hdf_handle* h, const float* h_mu, int K, void* stream);
 
+/* Change the widths of the filter for the following calls: omega of Sec. III
+ * takes sigma_s and phi takes sigma_r, while the window half-width S, the
+ * centres and every buffer stay.  The spatial taps (or, for the recursive
+ * Gaussian, the recursion's coefficients) are taken from sigma_s at each
+ * launch; A = [phi(mu_k - mu_l)] of Eq. (12) depends on sigma_r, so when the
+ * handle holds centres (after hdf_cluster or hdf_set_centers) A and A^+ are
+ * refitted on `stream` (asynchronous).  The clustering does not depend on the
+ * widths.  With S frozen, a sigma_s well above S/3 gives the Gaussian of that
+ * width truncated to W = [-S, S]^2 (Eq. (1)).  Allocates nothing: with it the
+ * gradient of hdf_backward with respect to log sigma_s and log sigma_r can
+ * drive an optimisation of the widths on one handle.
+ * Errors: HDF_EINVAL (NULL handle; a sigma <= 0 or not finite; sigma_s < 0.5
+ * with the recursive Gaussian), HDF_ECUDA. */
+hdf_status hdf_set_sigmas(hdf_handle* h, double sigma_s, double sigma_r, void* stream);
+
 /* Copy the centres (K_eff x rho float32) to h_mu (room for desc.K rows) and
  * K_eff to *K_eff.  Synchronises `stream`. */
 hdf_status hdf_get_centers(hdf_handle* h, float* h_mu, int* K_eff, void* stream);

@@ -49,6 +49,7 @@ SIGNATURES = [
     ("hdf_create", C.c_int, [C.POINTER(_P), C.POINTER(hdf_desc)]),
     ("hdf_destroy", None, [_P]),
     ("hdf_set_wait_limit", C.c_int, [_P, C.c_double]),
+    ("hdf_set_sigmas", C.c_int, [_P, C.c_double, C.c_double, _P]),
     ("hdf_set_stage_timing", C.c_int, [_P, C.c_int]),
     ("hdf_get_stage_times", C.c_int, [_P, _P, C.c_int, C.POINTER(C.c_int)]),
     ("hdf_get_desc", C.c_int, [_P, C.POINTER(hdf_desc)]),

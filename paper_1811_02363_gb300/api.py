@@ -148,12 +148,16 @@ class HDFilter:
                                      _stream()), "hdf_backward")
         return gf, gs[0], gs[1]
 
-    def _check_sigmas(self, log_sigma_s: float, log_sigma_r: float) -> None:
-        for name, lv, ref in (("sigma_s", log_sigma_s, self.desc.sigma_s),
-                              ("sigma_r", log_sigma_r, self.desc.sigma_r)):
-            if abs(math.exp(lv) - ref) > 1e-6 * ref:   # float32 log-sigma tensors
-                raise ValueError(f"{name}={math.exp(lv)} differs from the filter's {ref}; "
-                                 "create a filter for the new value")
+    def set_sigmas(self, sigma_s: float, sigma_r: float) -> None:
+        """New sigma_s and sigma_r for the following calls (hdf_set_sigmas:
+        S, the centres and the buffers stay; A^+ is refitted on the device)."""
+        L.check(L.lib().hdf_set_sigmas(self._h, float(sigma_s), float(sigma_r), _stream()),
+                "hdf_set_sigmas")
+        self.desc.sigma_s, self.desc.sigma_r = float(sigma_s), float(sigma_r)
+
+    def _use_sigmas(self, sigma_s: float, sigma_r: float) -> None:
+        if sigma_s != self.desc.sigma_s or sigma_r != self.desc.sigma_r:
+            self.set_sigmas(sigma_s, sigma_r)
 
     def nlm_guide(self, f: torch.Tensor, patch: int = 7, out: torch.Tensor | None = None) -> torch.Tensor:
         """PCA-reduced patch guide (desc.rho features) of the image f (n, H, W)."""
@@ -247,7 +251,9 @@ class _FastFilterFn(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, f, log_sigma_s, log_sigma_r, flt, guide):
-        flt._check_sigmas(float(log_sigma_s), float(log_sigma_r))
+        ctx.sigmas = (math.exp(float(log_sigma_s)), math.exp(float(log_sigma_r)))
+        ctx.dtypes = (log_sigma_s.dtype, log_sigma_r.dtype)
+        flt._use_sigmas(*ctx.sigmas)
         p = f if guide is None else guide
         g = flt.apply(f.contiguous(), p)
         ctx.flt = flt
@@ -259,15 +265,19 @@ class _FastFilterFn(torch.autograd.Function):
     def backward(ctx, grad_g):
         (f,) = ctx.saved_tensors
         p = f if ctx.guide is None else ctx.guide
+        ctx.flt._use_sigmas(*ctx.sigmas)    # the widths of this forward call
         gf, gls, glr = ctx.flt.backward(f.contiguous(), p, grad_g.contiguous())
-        return gf, gls.to(torch.float32), glr.to(torch.float32), None, None
+        return gf, gls.to(ctx.dtypes[0]), glr.to(ctx.dtypes[1]), None, None
 
 
 def fast_filter(f: torch.Tensor, log_sigma_s: torch.Tensor, log_sigma_r: torch.Tensor,
                 flt: HDFilter, guide: torch.Tensor | None = None) -> torch.Tensor:
     """Differentiable fast filter (Algorithm 1) with the centres installed in
-    ``flt``.  ``exp(log_sigma_*)`` must equal the filter's sigmas (the handle
-    fixes them and S); gradients flow to f, log_sigma_s and log_sigma_r."""
+    ``flt``.  The widths exp(log_sigma_s), exp(log_sigma_r) are live: a call
+    whose values differ from the handle's installs them (hdf_set_sigmas: S
+    and the centres stay, A^+ is refitted), so their gradients can drive an
+    optimisation of the widths; gradients flow to f, log_sigma_s and
+    log_sigma_r."""
     return _FastFilterFn.apply(f, log_sigma_s, log_sigma_r, flt, guide)
 
 

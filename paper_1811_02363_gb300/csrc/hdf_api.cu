@@ -227,6 +227,17 @@ hdf_status hdf_cluster(hdf_handle* h, const void* d_p, void* stream) {
   }
   hdf::NvtxRange r("hdf cluster: fit A, A^+");
   HDF_CUDA(hdf::launch_fit(h, st), "fit");
+  h->has_centers = 1;
+  return HDF_OK;
+}
+
+hdf_status hdf_set_sigmas(hdf_handle* h, double sigma_s, double sigma_r, void* stream) {
+  if (!h || !(sigma_s > 0.0) || !(sigma_r > 0.0) || !isfinite(sigma_s) || !isfinite(sigma_r))
+    return HDF_EINVAL;
+  if (h->d.spatial == HDF_SPATIAL_YOUNG && !(sigma_s >= 0.5)) return HDF_EINVAL;
+  h->d.sigma_s = sigma_s;
+  h->d.sigma_r = sigma_r;
+  if (h->has_centers) HDF_CUDA(hdf::launch_fit(h, (cudaStream_t)stream), "set_sigmas fit");
   return HDF_OK;
 }
 
@@ -237,6 +248,7 @@ hdf_status hdf_set_centers(hdf_handle* h, const float* h_mu, int K, void* stream
   HDF_CUDA(cudaMemcpyAsync(h->mu, h_mu, bytes, cudaMemcpyHostToDevice, st), "set_centers copy");
   HDF_CUDA(hdf::launch_set_int(h->ctrl + hdf::CTRL_K_EFF, K, st), "set_centers K");
   HDF_CUDA(hdf::launch_fit(h, st), "fit");
+  h->has_centers = 1;
   return HDF_OK;
 }
 

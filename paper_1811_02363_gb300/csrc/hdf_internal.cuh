@@ -93,6 +93,7 @@ struct hdf_handle {
   // maps, after them, after the convolution tile kernel, after the last stage
   int timing;
   cudaEvent_t tev[4];
+  int has_centers;    // centres present (hdf_cluster / hdf_set_centers ran)
 };
 
 namespace hdf {

@@ -136,3 +136,78 @@ def test_backward_equals_brute_force_gradients_at_exactness(api):
     assert np.max(np.abs(gf - bf)) <= RTOL * scale
     assert abs(float(gls) - bls) <= RTOL * max(abs(bls), 1e-3 * scale)
     assert abs(float(glr) - blr) <= RTOL * max(abs(blr), 1e-3 * scale)
+
+
+def test_set_sigmas_equals_a_handle_made_for_the_widths(api):
+    """hdf_set_sigmas on a clustered handle (S and the centres kept, A^+
+    refitted) gives bit for bit the filter of a handle created with the new
+    widths, the same S and the same centres, and Algorithm 1 of the oracle at
+    the new widths."""
+    f = synthetic.color_rectangles(72, 61, seed=92)
+    f = np.clip(f + np.random.default_rng(93).normal(0, 0.03, f.shape), 0, 1).astype(np.float32)
+    fd = torch.from_numpy(f).cuda()
+    S = 6
+    flt = api.HDFilter(72, 61, 3, 3, 8, 2.0, 0.2, S=S)
+    flt.cluster(fd)
+    mu = flt.get_centers()
+    flt.set_sigmas(2.6, 0.12)
+    assert (flt.desc.sigma_s, flt.desc.sigma_r, flt.S) == (2.6, 0.12, S)
+    g1 = flt.apply(fd, fd)
+    ref = api.HDFilter(72, 61, 3, 3, mu.shape[0], 2.6, 0.12, S=S)
+    ref.set_centers(mu)
+    g2 = ref.apply(fd, fd)
+    assert torch.equal(g1, g2)
+    assert np.array_equal(flt.get_pinv(), ref.get_pinv())
+    want = O.fast_filter(f.astype(np.float64), f.astype(np.float64), mu.astype(np.float64), 2.6, 0.12, S)
+    assert np.max(np.abs(g1.cpu().numpy() - want)) <= 1e-4
+    with pytest.raises(Exception):
+        flt.set_sigmas(float("nan"), 0.1)
+    with pytest.raises(Exception):
+        flt.set_sigmas(1.0, 0.0)
+
+
+def test_autograd_with_live_sigmas(api):
+    """fast_filter installs the widths of its log-sigma inputs: the gradients
+    at widths other than the handle's match the FP64 reference at those
+    widths (S fixed), and a small step of log sigma_r against its gradient
+    lowers the loss."""
+    f = synthetic.color_rectangles(40, 36, seed=94)
+    f = np.clip(f + np.random.default_rng(95).normal(0, 0.03, f.shape), 0, 1).astype(np.float32)
+    mu = O.bisecting_kmeans(f.reshape(3, -1).T.astype(np.float64), 5)[0].astype(np.float32)
+    flt = api.HDFilter(40, 36, 3, 3, 5, 1.3, 0.35)
+    S = flt.S
+    flt.set_centers(mu)
+    G = np.random.default_rng(96).normal(size=f.shape).astype(np.float32)
+    fd = torch.from_numpy(f).cuda().requires_grad_(True)
+    ss, sr = 1.1, 0.28
+    ls = torch.tensor(math.log(ss), device="cuda", dtype=torch.float64, requires_grad=True)
+    lr = torch.tensor(math.log(sr), device="cuda", dtype=torch.float64, requires_grad=True)
+    g = api.fast_filter(fd, ls, lr, flt)
+    (g * torch.from_numpy(G).cuda()).sum().backward()
+    gf_ref, gls_ref, glr_ref, g_ref = OG.grads(f.astype(np.float64), None, mu.astype(np.float64),
+                                               ss, sr, S, G.astype(np.float64))
+    assert np.max(np.abs(g.detach().cpu().numpy() - g_ref)) <= 1e-4
+    scale = np.abs(gf_ref).max()
+    assert np.max(np.abs(fd.grad.cpu().numpy() - gf_ref)) <= RTOL * scale
+    assert abs(float(ls.grad) - gls_ref) <= RTOL * max(abs(gls_ref), 1e-3 * scale)
+    assert abs(float(lr.grad) - glr_ref) <= RTOL * max(abs(glr_ref), 1e-3 * scale)
+    assert ls.grad.dtype == torch.float64
+
+    # descent on log sigma_r towards the output at sigma_r = 0.2
+    target = O.fast_filter(f.astype(np.float64), f.astype(np.float64), mu.astype(np.float64),
+                           1.3, 0.2, S)
+    tgt = torch.from_numpy(target.astype(np.float32)).cuda()
+    fx = torch.from_numpy(f).cuda()
+    ls0 = torch.tensor(math.log(1.3), device="cuda")
+
+    def loss_and_grad(v):
+        lr_t = torch.tensor(v, device="cuda", requires_grad=True)
+        L = ((api.fast_filter(fx, ls0, lr_t, flt) - tgt) ** 2).sum()
+        L.backward()
+        return float(L), float(lr_t.grad)
+
+    v = math.log(0.35)
+    L0, d0 = loss_and_grad(v)
+    assert d0 > 0                                   # the loss grows with sigma_r above 0.2
+    L1, _ = loss_and_grad(v - 0.1 * math.copysign(1.0, d0))
+    assert L1 < L0

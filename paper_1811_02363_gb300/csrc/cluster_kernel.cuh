@@ -55,6 +55,11 @@ namespace {
 // SM): the instantiations for guides of few dimensions keep few coordinates
 // per point in registers and run 32 warps per SM; those for many dimensions
 // run fewer, larger threads.  A chunk is CH points, PPT per thread.
+// Lloyd passes: 1 = each thread tests its own points, margins prefetched one
+// chunk ahead; 0 = the points that need the full test compacted per chunk.
+#ifndef HDF_CL_DIRECT
+#define HDF_CL_DIRECT 1
+#endif
 #ifndef HDF_CL_THREADS
 #define HDF_CL_THREADS 256
 #endif
@@ -633,6 +638,19 @@ __host__ __device__ constexpr size_t dyn_red_offset(int rho) {
 __host__ __device__ constexpr size_t dyn_smem_bytes(int rho) {
   return ((dyn_red_offset(rho) + 127) / 128) * 128 +
          sizeof(float) * ((size_t)MAXG * record_floats(rho) + 2 * CL_THREADS);
+}
+
+// Lloyd passes of guides of up to 8 dimensions keep the margins (rounded
+// down to half precision: the skip test stays conservative) and sides of the
+// block's points in shared memory for the whole Lloyd loop of a round, when
+// the block holds at most RES_CHUNKS chunks.
+constexpr int RES_CHUNKS = 16;
+template <int RMAX>
+__host__ __device__ constexpr size_t resident_bytes() {
+  return RMAX <= 8 ? (size_t)RES_CHUNKS * CH * (sizeof(unsigned short) + 1) : 0;
+}
+__host__ __device__ constexpr size_t dyn_stage_offset(int rho) {
+  return (dyn_smem_bytes(rho) + 127) / 128 * 128;
 }
 
 // Distance statistics of every segment of the table against the centres
@@ -1253,7 +1271,8 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
         };
         // The full test of one point of split seg with coordinates x: nearer
         // centre (FP64 within 2^-14 of a tie), new margin, side change, sums.
-        auto test_point = [&](int seg, int pos, const float (&x)[RMAX]) {
+        // Returns the new margin; stores a side change (and its iteration).
+        auto test_point = [&](int seg, int pos, const float (&x)[RMAX], int sdp, int& sd_out) -> float {
           const float cum = (float)s.cum[seg];
           const float* ca = c32 + (2 * seg) * rho;
           const float* cb = ca + rho;
@@ -1282,8 +1301,8 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
             sd = e_b < e_a;
           }
           const float ra = sqrtf(da), rb = sqrtf(db);
-          a.marg[pos] = fabsf(rb - ra) - MARGIN_REL * (ra + rb) - s.cabs[seg] + cum;
-          const int sdp = (it > 0) ? (int)__ldcg(a.side + pos) : -1;
+          const float marg = fabsf(rb - ra) - MARGIN_REL * (ra + rb) - s.cabs[seg] + cum;
+          sd_out = (int)sd;
           if ((int)sd != sdp) {
             a.side[pos] = (uint8_t)sd;
             a.side[N + pos] = (uint8_t)(it + 1);   // iteration of the last change
@@ -1302,6 +1321,7 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
             for (int d = 0; d < RMAX; ++d)
               if (d < rho) two_sum_acc(hi[d], lo[d], sd ? x[d] : -x[d]);
           }
+          return marg;
         };
         auto flush_split = [&](int seg) {
           if (!s.seg_act[seg]) return;   // converged split: no record, no arrival
@@ -1318,6 +1338,88 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
           chg = 0;
           arrive(seg);
         };
+      const int nmine = bid < s.nchunks ? (s.nchunks - bid + a.G - 1) / a.G : 0;
+      bool resident = false;
+#if HDF_CL_DIRECT
+      if constexpr (resident_bytes<RMAX>() > 0) resident = nmine <= RES_CHUNKS;
+      if constexpr (resident_bytes<RMAX>() > 0) if (resident) {
+        // Each thread tests its own points.  Their margins and sides live in
+        // shared memory (slot c of the block's c-th chunk), so the margin
+        // test reads no global memory; the points that fail it are taken in
+        // batches of HB from groups of up to 4 chunks of one split, their
+        // coordinates loaded together (one round trip per batch).
+        constexpr int HB = RMAX <= 4 ? 8 : 4;
+        unsigned short* rmarg = (unsigned short*)(dyn + dyn_stage_offset(rho));
+        unsigned char* rside = (unsigned char*)(rmarg + (size_t)RES_CHUNKS * CH);
+        int cur = -1, sg = 0;
+        for (int c = 0; c < nmine;) {
+          const int j = bid + c * a.G;
+          while (s.seg_chunk0[sg + 1] <= j) ++sg;
+          if (sg != cur) {
+            if (cur >= 0) flush_split(cur);
+            cur = sg;
+          }
+          int ng = 1;
+          while (ng < 4 && c + ng < nmine && s.seg_chunk0[sg + 1] > j + ng * a.G) ++ng;
+          if (!s.seg_act[sg]) {   // uniform: shared flag
+            c += ng;
+            continue;
+          }
+          const int base0 = s.seg_start[sg] + (j - s.seg_chunk0[sg]) * CH;
+          const int end = s.seg_start[sg] + s.seg_count[sg];
+          const float cum = (float)s.cum[sg];
+          // bit k * PPT + u: point u of chunk c + k fails the margin test
+          unsigned hm = 0u;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+#pragma unroll
+            for (int u = 0; u < PPT; ++u) {
+              const int p = u * CL_THREADS + tid;
+              const int pos = base0 + k * a.G * CH + p;
+              if (k < ng && pos < end) {
+                bool hv = true;
+                if (it > 0) {
+                  const float m0 = __half2float(__ushort_as_half(rmarg[(size_t)(c + k) * CH + p]));
+                  hv = !(m0 - cum > 1e-6f * (fabsf(m0) + cum));
+                }
+                if (hv) hm |= 1u << (k * PPT + u);
+              }
+            }
+          }
+          while (hm) {
+            int slot[HB], pos[HB], sdp[HB];
+            float x[HB][RMAX];
+#pragma unroll
+            for (int b = 0; b < HB; ++b) {
+              slot[b] = -1;
+              if (hm) {
+                const int bit = __ffs(hm) - 1;
+                hm &= hm - 1u;
+                const int k = bit / PPT, u = bit % PPT;
+                const int p = u * CL_THREADS + tid;
+                slot[b] = (c + k) * CH + p;
+                pos[b] = base0 + k * a.G * CH + p;
+              }
+              sdp[b] = (slot[b] >= 0 && it > 0) ? (int)rside[slot[b]] : -1;
+#pragma unroll
+              for (int d = 0; d < RMAX; ++d)
+                x[b][d] = (slot[b] >= 0 && d < rho) ? xat(X, N, d, pos[b]) : 0.0f;
+            }
+#pragma unroll
+            for (int b = 0; b < HB; ++b) {
+              if (slot[b] < 0) continue;
+              int sd;
+              const float m = test_point(sg, pos[b], x[b], sdp[b], sd);
+              rmarg[slot[b]] = __half_as_ushort(__float2half_rd(m));
+              rside[slot[b]] = (unsigned char)sd;
+            }
+          }
+          c += ng;
+        }
+        if (cur >= 0) flush_split(cur);
+      }
+#endif
+      if (!resident) {
         // compact each chunk's points that need the full test in position
         // order (coalesced coordinate loads where they are dense) and spread
         // them over the block
@@ -1346,11 +1448,16 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
                 }
 #pragma unroll
                 for (int b = 0; b < UB; ++b)
-                  if (hp[b] >= 0) test_point(seg, hp[b], x[b]);
+                  if (hp[b] >= 0) {
+                    int sd;
+                    a.marg[hp[b]] = test_point(seg, hp[b], x[b],
+                                               it > 0 ? (int)__ldcg(a.side + hp[b]) : -1, sd);
+                  }
               }
               __syncthreads();   // hlist is reused by the next chunk
             },
             flush_split);
+      }
       }
       // finish the splits this block is the finishing block of
       for (int sl = 0; sl < s.nslots; ++sl) {
@@ -1654,7 +1761,7 @@ template <int RMAX>
 cudaError_t launch_cl(const ClArgs* table, const int4* groups, int ngroups, const int* order,
                       const void* p_override, int rho_max, int grid, unsigned long long wait_ns,
                       cudaStream_t st) {
-  const size_t smem = dyn_smem_bytes(rho_max);
+  const size_t smem = dyn_stage_offset(rho_max) + resident_bytes<RMAX>();
   cudaError_t e = cudaFuncSetAttribute(cluster_kernel<RMAX>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -97,6 +97,9 @@ struct ClShared {
   int hlist[CH];          // positions of a chunk that need the full test
   int wtab[PPT * CL_WARPS];   // per (u, warp) counts, then their exclusive prefix
   int wtotal;
+  int ccnt[4];               // side-b counts of a group of chunks (partition count pass)
+  int mypre[64];             // partition: side-b points before each of the block's chunks
+  int segpre[MAXSEG];        //   and before each segment's first chunk
   float segmax[MAXSEG];
   float slack[MAXACT];   // centre movement of the last update
   double cum[MAXACT];    // total centre movement since the split started
@@ -1540,41 +1543,103 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
       return before + x - v;
     };
     {
+      // side-b counts of the block's chunks, 4 chunks per round of loads;
+      // warp sums added up in shared memory (integer: order-free)
+      if (tid < 4) s.ccnt[tid] = 0;
+      __syncthreads();
       int seg = 0;
-      for (int j = bid; j < s.nchunks; j += a.G) {
-        int base, end;
-        chunk_geom(j, seg, base, end);
-        const int rv = s.slot[seg].rev_it + 1;   // 0: nothing undone
-        int c = 0;
+      for (int j0 = bid; j0 < s.nchunks; j0 += 4 * a.G) {
+        int c[4];
 #pragma unroll
-        for (int u = 0; u < PPT; ++u) {
-          const int pos = base + u * CL_THREADS + tid;
-          if (pos < end) c += accepted_side(a, pos, rv);
+        for (int k = 0; k < 4; ++k) {
+          const int j = j0 + k * a.G;
+          c[k] = 0;
+          if (j < s.nchunks) {
+            int base, end;
+            chunk_geom(j, seg, base, end);
+            const int rv = s.slot[seg].rev_it + 1;   // 0: nothing undone
+#pragma unroll
+            for (int u = 0; u < PPT; ++u) {
+              const int pos = base + u * CL_THREADS + tid;
+              if (pos < end) c[k] += accepted_side(a, pos, rv);
+            }
+          }
         }
-        int total;
-        block_scan(c, total);
-        if (tid == 0) a.chunk_cnt[j] = total;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int w = __reduce_add_sync(0xffffffffu, c[k]);
+          if ((tid & 31) == 0 && w != 0) atomicAdd(&s.ccnt[k], w);
+        }
+        __syncthreads();
+        if (tid < 4) {
+          const int j = j0 + tid * a.G;
+          if (j < s.nchunks) a.chunk_cnt[j] = s.ccnt[tid];
+          s.ccnt[tid] = 0;
+        }
+        __syncthreads();
       }
     }
     if (!grid_barrier(a, gen, s, TR_COUNT)) return;
     {
+      // Side-b points before each of the block's chunks within its segment,
+      // from one block scan of the whole count table: P[q] = sum of the
+      // counts of the chunks before q; the segment's share is
+      // P[j] - P[first chunk of the segment].  Blocks with more than
+      // MAXMINE chunks add the counts up chunk by chunk instead.
+      constexpr int MAXMINE = 64;
+      const int nmine = bid < s.nchunks ? (s.nchunks - bid + a.G - 1) / a.G : 0;
+      const bool tab = nmine <= MAXMINE;
+      if (tab) {
+        const int R = (s.nchunks + CL_THREADS - 1) / CL_THREADS;
+        const int q0 = tid * R < s.nchunks ? tid * R : s.nchunks;
+        const int q1 = q0 + R < s.nchunks ? q0 + R : s.nchunks;
+        int loc = 0;
+        for (int q = q0; q < q1; ++q) loc += __ldcg(a.chunk_cnt + q);
+        int total;
+        int pq = block_scan(loc, total);
+        for (int sg = 0; sg < s.nseg; ++sg) {
+          const int q = s.seg_chunk0[sg];
+          if (q == s.nchunks && tid == 0) s.segpre[sg] = total;
+        }
+        for (int q = q0; q < q1; ++q) {
+          if (q >= bid && (q - bid) % a.G == 0) s.mypre[(q - bid) / a.G] = pq;
+          for (int sg = 0; sg < s.nseg; ++sg)
+            if (s.seg_chunk0[sg] == q) s.segpre[sg] = pq;
+          pq += __ldcg(a.chunk_cnt + q);
+        }
+        __syncthreads();
+      }
       int seg = 0;
       for (int j = bid; j < s.nchunks; j += a.G) {
         int base, end;
         chunk_geom(j, seg, base, end);
         const SlotRec& sl = s.slot[seg];
         const int rv = sl.rev_it + 1;
-        // side-b points in the earlier chunks of this segment
-        int pb = 0;
-        for (int q = s.seg_chunk0[seg] + tid; q < j; q += CL_THREADS) pb += __ldcg(a.chunk_cnt + q);
         int before_b_chunk;
-        block_scan(pb, before_b_chunk);
+        if (tab) {
+          before_b_chunk = s.mypre[(j - bid) / a.G] - s.segpre[seg];
+        } else {
+          // side-b points in the earlier chunks of this segment
+          int pb = 0;
+          for (int q = s.seg_chunk0[seg] + tid; q < j; q += CL_THREADS) pb += __ldcg(a.chunk_cnt + q);
+          block_scan(pb, before_b_chunk);
+        }
         bool sdv[PPT];
         int rk[PPT];
+        // guides of up to 8 dimensions: the coordinates and raster indices are
+        // loaded together with the sides, before the ranks
+        constexpr bool EARLY = RMAX <= 8;
+        float xe[EARLY ? PPT : 1][RMAX];
+        uint32_t pe[EARLY ? PPT : 1];
 #pragma unroll
         for (int u = 0; u < PPT; ++u) {
           const int pos = base + u * CL_THREADS + tid;
           sdv[u] = (pos < end) && accepted_side(a, pos, rv) != 0;
+          if constexpr (EARLY) {
+            pe[u] = pos < end ? __ldcg(P + pos) : 0u;
+#pragma unroll
+            for (int d = 0; d < RMAX; ++d) xe[u][d] = (pos < end && d < rho) ? xat(X, N, d, pos) : 0.0f;
+          }
         }
         position_ranks(sdv, rk, s);
         const int cnt_a = sl.count - sl.cnt_b_acc;
@@ -1592,26 +1657,38 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
             np[u] = -1;
           }
         }
+        if constexpr (EARLY) {
 #pragma unroll
-        for (int u0 = 0; u0 < PPT; u0 += UB) {
-          float x[UB][RMAX];
-          uint32_t pid[UB];
-#pragma unroll
-          for (int b = 0; b < UB; ++b) {
-            const int pos = base + (u0 + b) * CL_THREADS + tid;
-            const bool v = np[u0 + b] >= 0;
-            pid[b] = v ? __ldcg(P + pos) : 0u;
-#pragma unroll
-            for (int d = 0; d < RMAX; ++d) x[b][d] = (v && d < rho) ? xat(X, N, d, pos) : 0.0f;
-          }
-#pragma unroll
-          for (int b = 0; b < UB; ++b) {
-            const int q = np[u0 + b];
+          for (int u = 0; u < PPT; ++u) {
+            const int q = np[u];
             if (q < 0) continue;
-            Pn[q] = pid[b];
+            Pn[q] = pe[u];
 #pragma unroll
             for (int d = 0; d < RMAX; ++d)
-              if (d < rho) Xn[(size_t)d * N + q] = x[b][d];
+              if (d < rho) Xn[(size_t)d * N + q] = xe[u][d];
+          }
+        } else {
+#pragma unroll
+          for (int u0 = 0; u0 < PPT; u0 += UB) {
+            float x[UB][RMAX];
+            uint32_t pid[UB];
+#pragma unroll
+            for (int b = 0; b < UB; ++b) {
+              const int pos = base + (u0 + b) * CL_THREADS + tid;
+              const bool v = np[u0 + b] >= 0;
+              pid[b] = v ? __ldcg(P + pos) : 0u;
+#pragma unroll
+              for (int d = 0; d < RMAX; ++d) x[b][d] = (v && d < rho) ? xat(X, N, d, pos) : 0.0f;
+            }
+#pragma unroll
+            for (int b = 0; b < UB; ++b) {
+              const int q = np[u0 + b];
+              if (q < 0) continue;
+              Pn[q] = pid[b];
+#pragma unroll
+              for (int d = 0; d < RMAX; ++d)
+                if (d < rho) Xn[(size_t)d * N + q] = x[b][d];
+            }
           }
         }
       }

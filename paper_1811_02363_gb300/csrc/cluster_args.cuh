@@ -13,6 +13,11 @@ constexpr int MAXSEG = 2 * MAXACT;
 constexpr int MAXNODES = 16 * HDF_MAX_K;
 constexpr int MAX_LLOYD = 20;
 constexpr int MAXG = 160;               // blocks of one group (one per SM)
+// Partial-record regions of a guide's workspace (each G x MAXSEG records):
+// 0 the distance passes, 1 and 2 the Lloyd passes of even and odd
+// iterations (region 2 also the root sums).  A region is rewritten only
+// after a grid barrier that every reader of its previous contents has passed.
+constexpr int PF_REGIONS = 3;
 constexpr unsigned long long DEFAULT_WAIT_NS = kDefaultWaitNs;
 constexpr float TIE_REL = 1.0f / 16384.0f;      // 2^-14: Lloyd recheck band
 constexpr float CAND_REL = 1.0f / 4096.0f;      // 2^-12: farthest-point candidates

@@ -867,6 +867,9 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
   double* acc_sum = tmp + MAXACT * (rho + 2);                 // MAXACT x rho
   double* nsum = acc_sum + MAXACT * rho;                      // MAXACT x rho sums of the split nodes
   double* mean_a = nsum + MAXACT * rho;                       // MAXACT x rho
+  // partial-record regions (distance passes; Lloyd even / odd iterations)
+  const size_t pf_stride = (size_t)a.G * MAXSEG * PS;
+  float* const pf_root = a.pf + 2 * pf_stride;
   auto acc_sum_a = [&](int i, int d) -> double& { return mean_a[i * rho + d]; };
   float* red = (float*)(dyn + ((dyn_red_offset(rho) + 127) / 128) * 128);   // MAXG records
   float* parts = red + (size_t)MAXG * PS;                                    // CL_THREADS pairs
@@ -930,7 +933,7 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
           }
         },
         [&](int seg) {
-          block_sum_f2<RMAX>(hi, lo, rho, s, a.pf + ((size_t)bid * MAXSEG + seg) * PS);
+          block_sum_f2<RMAX>(hi, lo, rho, s, pf_root + ((size_t)bid * MAXSEG + seg) * PS);
 #pragma unroll
           for (int d = 0; d < RMAX; ++d) hi[d] = lo[d] = 0.0f;
         });
@@ -938,7 +941,7 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
   if (!grid_barrier(a, gen, s, TR_ROOT)) return;
   replay<8>(rho, F2{0.0f, 0.0f}, [&](int) { return contrib_count(a, s, 0); },
       [&](int d, int i) {
-        const float* q = a.pf + ((size_t)contrib_block(a, s, 0, i) * MAXSEG) * PS + 2 * d;
+        const float* q = pf_root + ((size_t)contrib_block(a, s, 0, i) * MAXSEG) * PS + 2 * d;
         return F2{__ldcg(q), __ldcg(q + 1)};
       },
       [](F2 x, F2 y) { return f2_add(x, y); },
@@ -1104,7 +1107,7 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
     // Bulk copies of the nc partial records of split i (record of contributor
     // c at block contrib_block(c)) into dst, completed on the block's mbarrier;
     // bounded wait.  False (device status set) if the copies did not land.
-    auto stage_records = [&](int i, int nc, float* dst) -> bool {
+    auto stage_records = [&](int i, int it, int nc, float* dst) -> bool {
       const unsigned bytes = (unsigned)(PS * sizeof(float));
       if (tid == 0) {
         fence_proxy_async();   // earlier generic accesses before the async writes
@@ -1113,7 +1116,8 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
       __syncthreads();
       for (int c = tid; c < nc; c += CL_THREADS) {
         const size_t off = (size_t)contrib_block(a, s, i, c) * MAXSEG + i;
-        bulk_copy_g2s(dst + (size_t)c * PS, a.pf + off * PS, bytes, &s.mbar);
+        bulk_copy_g2s(dst + (size_t)c * PS, a.pf + (1 + (it & 1)) * pf_stride + off * PS, bytes,
+                      &s.mbar);
       }
       if (tid == 0) {
         int ok = mbar_wait(&s.mbar, s.mb_phase, a.wait_ns);
@@ -1134,6 +1138,95 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
     // contributors, xor tree), decide the split's state, compute the new
     // centres (means of the two sides) and the distance they moved, and
     // publish all of it for the other blocks (read after the grid barrier).
+    // Lloyd update of split i from its reduced sums fin = tmp + i (rho + 2),
+    // by one warp (lanes over the coordinates): accept, revert or stop, the
+    // new FP64 centres and the movement bounds behind the skip test, then
+    // the state published to global memory for the other blocks.
+    auto update_split = [&](int i, int it, int lane) {
+      const double* fin = tmp + i * (rho + 2);
+      SlotRec& sl = s.slot[i];
+      int recompute = 0;
+      if (lane == 0) {
+        sl.recompute = 0;
+        const int cb = (it == 0 ? 0 : sl.cnt_b_acc) + (int)fin[rho];
+        const int changed = (int)fin[rho + 1];
+        if (it == 0 && (cb == 0 || cb == sl.count)) {          // degenerate pair: not splittable
+          sl.done = 1;
+          sl.split = 0;
+        } else if (it > 0 && (cb == 0 || cb == sl.count)) {    // a side would be empty:
+          sl.done = 1;                                          // keep the previous assignment
+          sl.rev_it = it;
+          sl.iters = it;
+        } else if (it > 0 && changed == 0) {                   // converged
+          sl.done = 1;
+          sl.iters = it;
+        } else {                                                // accept this assignment
+          sl.cnt_b_cur = cb;
+          sl.iters = it + 1;
+          sl.recompute = 1;
+          if (it + 1 == MAX_LLOYD) sl.done = 1;
+        }
+        recompute = sl.recompute;
+      }
+      __syncwarp();
+      recompute = __shfl_sync(0xffffffffu, recompute, 0);
+      if (recompute) {
+        // accepted sums, the new means (a, b) and the distance each centre moved
+        const double nb_cnt = (double)sl.cnt_b_cur, na_cnt = (double)(sl.count - sl.cnt_b_cur);
+        // The centres in FP64; the norms behind the skip bounds in FP32 (FP64
+        // issues at a small fraction of the FP32 rate).  Rounded up: the
+        // FP32 sums of <= 2 rho nonnegative terms and the square roots are
+        // within 2^-19 relative, covered by the factor 1 + 2^-16; squares
+        // that underflow lose less than 1e-18 in a norm, covered by the
+        // absolute 1e-18.  Upper bounds only decide which points are
+        // re-examined, never an assignment.
+        float ma2 = 0.0f, mb2 = 0.0f, na = 0.0f, nb = 0.0f;
+        for (int d = lane; d < rho; d += 32) {
+          const double sb = fin[d] + (it > 0 ? acc_sum[i * rho + d] : 0.0);
+          acc_sum[i * rho + d] = sb;
+          const double mb = quotient(sb, nb_cnt);
+          const double ma = quotient(nsum[i * rho + d] - sb, na_cnt);
+          const float ua = (float)(ma - c64[(2 * i) * rho + d]);
+          const float ub = (float)(mb - c64[(2 * i + 1) * rho + d]);
+          const float fa = (float)ma, fb = (float)mb;
+          ma2 = fmaf(ua, ua, ma2);
+          mb2 = fmaf(ub, ub, mb2);
+          na = fmaf(fa, fa, na);
+          nb = fmaf(fb, fb, nb);
+          c64[(2 * i) * rho + d] = ma;
+          c64[(2 * i + 1) * rho + d] = mb;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          ma2 += __shfl_xor_sync(0xffffffffu, ma2, o);
+          mb2 += __shfl_xor_sync(0xffffffffu, mb2, o);
+          na += __shfl_xor_sync(0xffffffffu, na, o);
+          nb += __shfl_xor_sync(0xffffffffu, nb, o);
+        }
+        if (lane == 0) {
+          constexpr float UP32 = 1.0f + 1.0f / 65536.0f;
+          s.slack[i] = (sqrtf(ma2) + sqrtf(mb2)) * UP32 + 1e-18f;
+          s.cum[i] = (s.cum[i] + (double)s.slack[i]) * ROUND_UP;
+          s.cabs[i] = (sqrtf(na) + sqrtf(nb)) * (UP32 / 1048576.0f);
+          sl.cnt_b_acc = sl.cnt_b_cur;
+        }
+      }
+      __syncwarp();
+      // publish
+      for (int v = lane; v < 3 * rho; v += 32) {
+        if (v < 2 * rho) a.gcen[(size_t)i * 2 * rho + v] = c64[2 * i * rho + v];
+        else a.gacc[(size_t)i * rho + v - 2 * rho] = acc_sum[i * rho + v - 2 * rho];
+      }
+      if (lane == 0) {
+        SlotOut o;
+        o.r = sl;
+        o.slack = s.slack[i];
+        o.cabs = s.cabs[i];
+        o.cum = s.cum[i];
+        a.sout[i] = o;
+      }
+    };
+
     auto finish_split = [&](int i, int it) -> bool {
       const int nc = contrib_count(a, s, i);
       const int V = rho + 2;
@@ -1141,7 +1234,7 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
       // flight at once), then reduce them in a fixed order: thread (g, v)
       // sums value v of the records c = g, g + NG, ... (ascending), and
       // fin[v] = ((part_0 + part_1) + ...) + part_{NG-1}.
-      if (!stage_records(i, nc, red)) return false;
+      if (!stage_records(i, it, nc, red)) return false;
       const int VS = V <= 32 ? 32 : (V <= 64 ? 64 : 128);   // value slots
       const int NG = CL_THREADS / VS;                        // record classes
       {
@@ -1165,91 +1258,8 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
         fin[v] = f2_to_d(t);
       }
       __syncthreads();
-      // the update, by warp 0 alone (lanes over the coordinates)
-      if (tid < 32) {
-        const int lane = tid;
-        SlotRec& sl = s.slot[i];
-        int recompute = 0;
-        if (lane == 0) {
-          sl.recompute = 0;
-          const int cb = (it == 0 ? 0 : sl.cnt_b_acc) + (int)fin[rho];
-          const int changed = (int)fin[rho + 1];
-          if (it == 0 && (cb == 0 || cb == sl.count)) {          // degenerate pair: not splittable
-            sl.done = 1;
-            sl.split = 0;
-          } else if (it > 0 && (cb == 0 || cb == sl.count)) {    // a side would be empty:
-            sl.done = 1;                                          // keep the previous assignment
-            sl.rev_it = it;
-            sl.iters = it;
-          } else if (it > 0 && changed == 0) {                   // converged
-            sl.done = 1;
-            sl.iters = it;
-          } else {                                                // accept this assignment
-            sl.cnt_b_cur = cb;
-            sl.iters = it + 1;
-            sl.recompute = 1;
-            if (it + 1 == MAX_LLOYD) sl.done = 1;
-          }
-          recompute = sl.recompute;
-        }
-        __syncwarp();
-        recompute = __shfl_sync(0xffffffffu, recompute, 0);
-        if (recompute) {
-          // accepted sums, the new means (a, b) and the distance each centre moved
-          const double nb_cnt = (double)sl.cnt_b_cur, na_cnt = (double)(sl.count - sl.cnt_b_cur);
-          // The centres in FP64; the norms behind the skip bounds in FP32 (FP64
-          // issues at a small fraction of the FP32 rate).  Rounded up: the
-          // FP32 sums of <= 2 rho nonnegative terms and the square roots are
-          // within 2^-19 relative, covered by the factor 1 + 2^-16; squares
-          // that underflow lose less than 1e-18 in a norm, covered by the
-          // absolute 1e-18.  Upper bounds only decide which points are
-          // re-examined, never an assignment.
-          float ma2 = 0.0f, mb2 = 0.0f, na = 0.0f, nb = 0.0f;
-          for (int d = lane; d < rho; d += 32) {
-            const double sb = fin[d] + (it > 0 ? acc_sum[i * rho + d] : 0.0);
-            acc_sum[i * rho + d] = sb;
-            const double mb = quotient(sb, nb_cnt);
-            const double ma = quotient(nsum[i * rho + d] - sb, na_cnt);
-            const float ua = (float)(ma - c64[(2 * i) * rho + d]);
-            const float ub = (float)(mb - c64[(2 * i + 1) * rho + d]);
-            const float fa = (float)ma, fb = (float)mb;
-            ma2 = fmaf(ua, ua, ma2);
-            mb2 = fmaf(ub, ub, mb2);
-            na = fmaf(fa, fa, na);
-            nb = fmaf(fb, fb, nb);
-            c64[(2 * i) * rho + d] = ma;
-            c64[(2 * i + 1) * rho + d] = mb;
-          }
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            ma2 += __shfl_xor_sync(0xffffffffu, ma2, o);
-            mb2 += __shfl_xor_sync(0xffffffffu, mb2, o);
-            na += __shfl_xor_sync(0xffffffffu, na, o);
-            nb += __shfl_xor_sync(0xffffffffu, nb, o);
-          }
-          if (lane == 0) {
-            constexpr float UP32 = 1.0f + 1.0f / 65536.0f;
-            s.slack[i] = (sqrtf(ma2) + sqrtf(mb2)) * UP32 + 1e-18f;
-            s.cum[i] = (s.cum[i] + (double)s.slack[i]) * ROUND_UP;
-            s.cabs[i] = (sqrtf(na) + sqrtf(nb)) * (UP32 / 1048576.0f);
-            sl.cnt_b_acc = sl.cnt_b_cur;
-          }
-        }
-        __syncwarp();
-        // publish
-        for (int v = lane; v < 3 * rho; v += 32) {
-          if (v < 2 * rho) a.gcen[(size_t)i * 2 * rho + v] = c64[2 * i * rho + v];
-          else a.gacc[(size_t)i * rho + v - 2 * rho] = acc_sum[i * rho + v - 2 * rho];
-        }
-        if (lane == 0) {
-          SlotOut o;
-          o.r = sl;
-          o.slack = s.slack[i];
-          o.cabs = s.cabs[i];
-          o.cum = s.cum[i];
-          a.sout[i] = o;
-        }
-      }
+      // the update, by warp 0 alone
+      if (tid < 32) update_split(i, it, tid);
       __syncthreads();
       return true;
     };
@@ -1258,6 +1268,7 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
     for (int it = 0; it < MAX_LLOYD; ++it) {
       const int all_done = __syncthreads_and(tid < s.nslots ? s.slot[tid].done : 1);
       if (all_done) break;
+      float* const lpf = a.pf + (1 + (it & 1)) * pf_stride;   // this iteration's records
       {
         // it == 0: full side-b sums; it > 0: change of the side-b sums (points
         // that switched), so that skipped points need no coordinates at all.
@@ -1330,10 +1341,10 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
           if (!s.seg_act[seg]) return;   // converged split: no record, no arrival
           const size_t off = (size_t)bid * MAXSEG + seg;
           if (__syncthreads_or(cnt != 0 || chg != 0)) {
-            block_sum_f2<RMAX>(hi, lo, rho, s, a.pf + off * PS);
-            block_sum_i2(cnt, chg, s, reinterpret_cast<int*>(a.pf + off * PS + 2 * rho));
+            block_sum_f2<RMAX>(hi, lo, rho, s, lpf + off * PS);
+            block_sum_i2(cnt, chg, s, reinterpret_cast<int*>(lpf + off * PS + 2 * rho));
           } else {   // nothing moved to or from side b here: a zero record
-            for (int v = tid; v < PS; v += CL_THREADS) a.pf[off * PS + v] = 0.0f;
+            for (int v = tid; v < PS; v += CL_THREADS) lpf[off * PS + v] = 0.0f;
           }
 #pragma unroll
           for (int d = 0; d < RMAX; ++d) hi[d] = lo[d] = 0.0f;

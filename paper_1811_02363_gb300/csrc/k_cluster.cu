@@ -49,7 +49,7 @@ Layout layout(int N, int rho, int G) {
   L.d32 = take(sizeof(float) * (size_t)N);
   L.nodes = take(sizeof(NodeRec) * MAXNODES);
   L.node_sum = take(sizeof(double) * MAXNODES * (size_t)rho);
-  L.pf = take(sizeof(float) * (size_t)G * MAXSEG * record_floats(rho));
+  L.pf = take(sizeof(float) * PF_REGIONS * (size_t)G * MAXSEG * record_floats(rho));
   L.pi = take(sizeof(int) * (size_t)G * MAXSEG * 2);
   L.pd = take(sizeof(float) * (size_t)G * MAXSEG);
   L.pdd = take(sizeof(double) * (size_t)G * MAXSEG);

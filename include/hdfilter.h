@@ -208,6 +208,19 @@ hdf_status hdf_backward(hdf_handle* h, const float* d_f, const void* d_p,
                         const float* d_grad_g, float* d_grad_f,
                         double* d_grad_log_sigma, void* stream);
 
+/* hdf_backward right after the forward pass: d_g is the output of the last
+ * hdf_apply on this handle, made from the same d_f and d_p (the caller
+ * vouches for that; their contents must not have changed), and the range
+ * maps, coefficients, denominators and guard list that apply left in the
+ * handle are used instead of being recomputed (saves the forward pass).  At
+ * the pixels that apply recomputed in FP64 the adjoint uses the FP64 value of
+ * g_hat.  Errors: HDF_EINVAL when the handle's last state-changing call was
+ * not hdf_apply (hdf_backward, hdf_cluster, hdf_set_centers and
+ * hdf_set_sigmas each end that state), plus those of hdf_backward. */
+hdf_status hdf_backward_after_apply(hdf_handle* h, const float* d_f, const void* d_p,
+                                    const float* d_g, const float* d_grad_g, float* d_grad_f,
+                                    double* d_grad_log_sigma, void* stream);
+
 /* hdf_apply for callers that cannot allocate device memory: a framework or
  * plug-in host that owns all device memory through its own pool and forbids
  * foreign allocations, or a latency-critical path where a cudaMalloc/cudaFree

@@ -60,6 +60,7 @@ SIGNATURES = [
     ("hdf_get_labels", C.c_int, [_P, _P, _P]),
     ("hdf_apply", C.c_int, [_P, _P, _P, _P, _P]),
     ("hdf_backward", C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    ("hdf_backward_after_apply", C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     ("hdf_nlm_guide", C.c_int, [_P, _P, C.c_int, _P, _P]),
     ("hdf_apply_static", C.c_int, [C.POINTER(hdf_desc), _P, C.c_int, _P, _P, _P, _P]),
     ("hdf_scale_guide", C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P, _P]),

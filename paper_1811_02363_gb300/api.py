@@ -67,6 +67,7 @@ class HDFilter:
         L.check(L.lib().hdf_create(C.byref(self._h), C.byref(self.desc)), "hdf_create")
         L.check(L.lib().hdf_get_desc(self._h, C.byref(self.desc)), "hdf_get_desc")
         self.guide_torch_dtype = torch.float32 if guide_dtype == "f32" else torch.bfloat16
+        self._seq = 0   # calls that change the handle's state (apply, cluster, backward, ...)
 
     # -- lifecycle
     def close(self) -> None:
@@ -98,6 +99,7 @@ class HDFilter:
     def cluster(self, p: torch.Tensor) -> None:
         self._check_guide(p)
         L.check(L.lib().hdf_cluster(self._h, _ptr(p), _stream()), "hdf_cluster")
+        self._seq += 1
 
     def set_centers(self, mu) -> None:
         mu = np.ascontiguousarray(np.asarray(mu, dtype=np.float32))
@@ -106,6 +108,7 @@ class HDFilter:
         self._mu_keepalive = mu
         L.check(L.lib().hdf_set_centers(self._h, mu.ctypes.data_as(C.c_void_p), mu.shape[0],
                                         _stream()), "hdf_set_centers")
+        self._seq += 1
         torch.cuda.current_stream().synchronize()
 
     def get_centers(self) -> np.ndarray:
@@ -135,17 +138,29 @@ class HDFilter:
         g = torch.empty_like(f) if out is None else out
         self._check_f(g, "out")
         L.check(L.lib().hdf_apply(self._h, _ptr(f), _ptr(p), _ptr(g), _stream()), "hdf_apply")
+        self._seq += 1
         return g
 
-    def backward(self, f: torch.Tensor, p: torch.Tensor, grad_g: torch.Tensor):
-        """Returns (dL/df, dL/dlog sigma_s, dL/dlog sigma_r) as CUDA tensors."""
+    def backward(self, f: torch.Tensor, p: torch.Tensor, grad_g: torch.Tensor,
+                 g: torch.Tensor | None = None):
+        """Returns (dL/df, dL/dlog sigma_s, dL/dlog sigma_r) as CUDA tensors.
+        With ``g`` (the output of the last ``apply`` of this filter, from the
+        same f and p) the forward state left by that apply is reused
+        (hdf_backward_after_apply) instead of recomputed."""
         self._check_f(f)
         self._check_guide(p)
         self._check_f(grad_g, "grad_g")
         gf = torch.empty_like(f)
         gs = torch.zeros(2, dtype=torch.float64, device=f.device)
-        L.check(L.lib().hdf_backward(self._h, _ptr(f), _ptr(p), _ptr(grad_g), _ptr(gf), _ptr(gs),
-                                     _stream()), "hdf_backward")
+        if g is None:
+            L.check(L.lib().hdf_backward(self._h, _ptr(f), _ptr(p), _ptr(grad_g), _ptr(gf),
+                                         _ptr(gs), _stream()), "hdf_backward")
+        else:
+            self._check_f(g, "g")
+            L.check(L.lib().hdf_backward_after_apply(self._h, _ptr(f), _ptr(p), _ptr(g),
+                                                     _ptr(grad_g), _ptr(gf), _ptr(gs), _stream()),
+                    "hdf_backward_after_apply")
+        self._seq += 1
         return gf, gs[0], gs[1]
 
     def set_sigmas(self, sigma_s: float, sigma_r: float) -> None:
@@ -153,6 +168,7 @@ class HDFilter:
         S, the centres and the buffers stay; A^+ is refitted on the device)."""
         L.check(L.lib().hdf_set_sigmas(self._h, float(sigma_s), float(sigma_r), _stream()),
                 "hdf_set_sigmas")
+        self._seq += 1
         self.desc.sigma_s, self.desc.sigma_r = float(sigma_s), float(sigma_r)
 
     def _use_sigmas(self, sigma_s: float, sigma_r: float) -> None:
@@ -258,15 +274,17 @@ class _FastFilterFn(torch.autograd.Function):
         g = flt.apply(f.contiguous(), p)
         ctx.flt = flt
         ctx.guide = guide
-        ctx.save_for_backward(f)
+        ctx.seq = flt._seq          # the handle still holds this apply's state while unchanged
+        ctx.save_for_backward(f, g)
         return g
 
     @staticmethod
     def backward(ctx, grad_g):
-        (f,) = ctx.saved_tensors
+        f, g = ctx.saved_tensors
         p = f if ctx.guide is None else ctx.guide
         ctx.flt._use_sigmas(*ctx.sigmas)    # the widths of this forward call
-        gf, gls, glr = ctx.flt.backward(f.contiguous(), p, grad_g.contiguous())
+        reuse = g if ctx.flt._seq == ctx.seq else None
+        gf, gls, glr = ctx.flt.backward(f.contiguous(), p, grad_g.contiguous(), g=reuse)
         return gf, gls.to(ctx.dtypes[0]), glr.to(ctx.dtypes[1]), None, None
 
 

@@ -228,6 +228,7 @@ hdf_status hdf_cluster(hdf_handle* h, const void* d_p, void* stream) {
   hdf::NvtxRange r("hdf cluster: fit A, A^+");
   HDF_CUDA(hdf::launch_fit(h, st), "fit");
   h->has_centers = 1;
+  h->after_apply = 0;
   return HDF_OK;
 }
 
@@ -237,6 +238,7 @@ hdf_status hdf_set_sigmas(hdf_handle* h, double sigma_s, double sigma_r, void* s
   if (h->d.spatial == HDF_SPATIAL_YOUNG && !(sigma_s >= 0.5)) return HDF_EINVAL;
   h->d.sigma_s = sigma_s;
   h->d.sigma_r = sigma_r;
+  h->after_apply = 0;
   if (h->has_centers) HDF_CUDA(hdf::launch_fit(h, (cudaStream_t)stream), "set_sigmas fit");
   return HDF_OK;
 }
@@ -249,6 +251,7 @@ hdf_status hdf_set_centers(hdf_handle* h, const float* h_mu, int K, void* stream
   HDF_CUDA(hdf::launch_set_int(h->ctrl + hdf::CTRL_K_EFF, K, st), "set_centers K");
   HDF_CUDA(hdf::launch_fit(h, st), "fit");
   h->has_centers = 1;
+  h->after_apply = 0;
   return HDF_OK;
 }
 
@@ -288,6 +291,7 @@ hdf_status hdf_apply(hdf_handle* h, const float* d_f, const void* d_p, float* d_
   if (!h || !d_f || !d_p || !d_g) return HDF_EINVAL;
   if ((const void*)d_g == (const void*)d_f || (const void*)d_g == d_p) return HDF_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
+  h->after_apply = 0;
   if (h->timing) HDF_CUDA(cudaEventRecord(h->tev[0], st), "timing event");
   {
     hdf::NvtxRange r("hdf apply: range maps");
@@ -300,6 +304,7 @@ hdf_status hdf_apply(hdf_handle* h, const float* d_f, const void* d_p, float* d_
   hdf::NvtxRange r("hdf apply: convolutions + combine");
   HDF_CUDA(hdf::launch_filter(h, d_f, d_p, d_g, st), "filter");
   if (h->timing) HDF_CUDA(cudaEventRecord(h->tev[3], st), "timing event");
+  h->after_apply = 1;
   return HDF_OK;
 }
 
@@ -309,7 +314,22 @@ hdf_status hdf_backward(hdf_handle* h, const float* d_f, const void* d_p, const 
   if (h->d.coef != HDF_COEF_OPT || h->d.spatial != HDF_SPATIAL_GAUSS) return HDF_EUNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   hdf::NvtxRange r("hdf backward");
+  h->after_apply = 0;   // the guard pixels' coefficient columns become one-hot
   HDF_CUDA(hdf::launch_backward(h, d_f, d_p, d_grad_g, d_grad_f, d_grad_log_sigma, st),
+           "backward");
+  return HDF_OK;
+}
+
+hdf_status hdf_backward_after_apply(hdf_handle* h, const float* d_f, const void* d_p,
+                                    const float* d_g, const float* d_grad_g, float* d_grad_f,
+                                    double* d_grad_log_sigma, void* stream) {
+  if (!h || !d_f || !d_p || !d_g || !d_grad_g || !d_grad_f || !d_grad_log_sigma) return HDF_EINVAL;
+  if (h->d.coef != HDF_COEF_OPT || h->d.spatial != HDF_SPATIAL_GAUSS) return HDF_EUNSUPPORTED;
+  if (!h->after_apply) return HDF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  hdf::NvtxRange r("hdf backward after apply");
+  h->after_apply = 0;
+  HDF_CUDA(hdf::launch_backward(h, d_f, d_p, d_grad_g, d_grad_f, d_grad_log_sigma, st, d_g),
            "backward");
   return HDF_OK;
 }

@@ -95,6 +95,7 @@ struct hdf_handle {
   int timing;
   cudaEvent_t tev[4];
   int has_centers;    // centres present (hdf_cluster / hdf_set_centers ran)
+  int after_apply;    // B, C, s, den and the guard list are those of the last hdf_apply
 };
 
 namespace hdf {
@@ -130,8 +131,11 @@ size_t nlm_workspace_bytes(int G);
 cudaError_t launch_nlm_guide(const float* f, int n, int H, int W, int m, int rho, float* p,
                              void* ws, size_t ws_bytes, int* ctrl, cudaStream_t st);
 cudaError_t cluster_trace(hdf_handle* h, long long* host, int cap, int* count, cudaStream_t st);
+// g_fwd: null = recompute the forward pass; else the output of the last apply
+// (whose B, C, s, den and guard list are still in the handle).
 cudaError_t launch_backward(hdf_handle* h, const float* f, const void* p, const float* G,
-                            float* grad_f, double* grad_ls, cudaStream_t st);
+                            float* grad_f, double* grad_ls, cudaStream_t st,
+                            const float* g_fwd = nullptr);
 
 // Host helpers.
 Taps make_taps(double sigma_s, int S, int spatial);   // omega_1 at [t + S], 0 beyond S

@@ -4,7 +4,8 @@
 // c(i) = A^{-1} b(i) (Eq. (11) for a full-rank A).
 //
 // Steps (all on `stream`, no allocation, no host synchronisation):
-//   1. forward recompute: range maps, filter -> g_hat, denominator D;
+//   1. forward recompute: range maps, filter -> g_hat, denominator D (skipped
+//      by hdf_backward_after_apply, which takes them from the last apply);
 //   2. pixels where the denominator guard fired use the indicator form
 //      (c = e_s, D = r_s): their coefficient columns become one-hot and they
 //      are flagged (no gradient through c there);
@@ -215,7 +216,7 @@ cudaError_t launch_final_r(hdf_handle* h, const float* f, const void* p, int gi,
 }  // namespace
 
 cudaError_t launch_backward(hdf_handle* h, const float* f, const void* p, const float* G,
-                            float* grad_f, double* grad_ls, cudaStream_t st) {
+                            float* grad_f, double* grad_ls, cudaStream_t st, const float* g_fwd) {
   const hdf_desc& d = h->d;
   const int SB = filter_bucket(d.S);
   if (SB < 0) return cudaErrorInvalidValue;
@@ -226,16 +227,21 @@ cudaError_t launch_backward(hdf_handle* h, const float* f, const void* p, const 
   const int ty = SB > 24 ? 32 : 64;            // tile height of the backward tile kernels
   const int ntiles = ((d.W + 31) / 32) * ((d.H + ty - 1) / ty);
   if (ntiles > PART_SIGMA_R) return cudaErrorInvalidValue;   // per-tile partials must fit
-  // 1. forward recompute (g_hat into scratch, D, guard list)
-  if ((e = launch_rangemap(h, p, st)) != cudaSuccess) return e;
-  if ((e = launch_filter(h, f, p, h->bw_g, st, 0)) != cudaSuccess) return e;
+  // 1. forward recompute (g_hat into scratch, D, guard list), unless the
+  //    handle still holds the state of the apply that produced g_fwd
+  const float* ghat = g_fwd;
+  if (!ghat) {
+    if ((e = launch_rangemap(h, p, st)) != cudaSuccess) return e;
+    if ((e = launch_filter(h, f, p, h->bw_g, st, 0)) != cudaSuccess) return e;
+    ghat = h->bw_g;
+  }
   // 2. guarded pixels
   if ((e = cudaMemsetAsync(h->bw_flag, 0, h->N, st)) != cudaSuccess) return e;
   const Taps exact = make_taps(d.sigma_s, d.S, d.spatial);
   bwd_fallback_kernel<<<sms, 256, 0, st>>>(h->B, h->s, h->fix_list, h->ctrl, d.H, d.W, d.K, d.S,
                                            exact, h->den, h->C, h->bw_flag);
   // 3. lambda planes
-  bwd_lambda_kernel<<<sms * 4, 256, 0, st>>>(G, h->bw_g, h->den, h->N, d.n, h->bw_lam);
+  bwd_lambda_kernel<<<sms * 4, 256, 0, st>>>(G, ghat, h->den, h->N, d.n, h->bw_lam);
   // 4./5. tile passes; omega_1 and omega_1' = omega_1 t^2 / sigma_s^2 centred in the bucket
   Taps t1, t2;
   for (int t = 0; t < 2 * HDF_MAX_S + 1; ++t) t1.w[t] = t2.w[t] = 0.0f;

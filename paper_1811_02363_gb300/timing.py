@@ -2,8 +2,10 @@
 
 For each workload: the PCA guide (nonlocal means), the clustering, the filter
 apply with the Gaussian, box and recursive-Gaussian spatial kernels, with
---bruteforce the brute force of Eq. (1)-(2), and with --backward the gradient pass (dL/df, dL/dlog sigma_s, dL/dlog sigma_r) of the
-Gaussian filter for a random upstream gradient.  Times are medians of CUDA
+--bruteforce the brute force of Eq. (1)-(2), and with --backward the gradient
+pass (dL/df, dL/dlog sigma_s, dL/dlog sigma_r) of the Gaussian filter for a
+random upstream gradient, on its own and right after the forward pass (whose
+state it then reuses).  Times are medians of CUDA
 events on the current stream, inputs resident on the device.
 
     python -m paper_1811_02363_gb300.timing hyper512 color2048 --backward --bruteforce
@@ -28,6 +30,24 @@ def median_ms(fn, reps: int = 10) -> float:
     torch.cuda.synchronize()
     ts = []
     for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        fn()
+        b.record(s)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
+
+
+def median_ms_after(pre, fn, reps: int = 10) -> float:
+    """Median ms of fn alone, each run preceded by an untimed pre()."""
+    s = torch.cuda.current_stream()
+    pre()
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        pre()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(s)
         fn()
@@ -64,6 +84,9 @@ def workload_times(name: str, backward: bool = False, bruteforce: bool = False) 
                 G = torch.randn(f.shape, device=f.device, dtype=f.dtype,
                                 generator=torch.Generator(device=f.device).manual_seed(5))
                 out["backward_ms"] = median_ms(lambda: flt.backward(f, p, G))
+                # right after the forward pass: its state reused (hdf_backward_after_apply)
+                out["backward_after_apply_ms"] = median_ms_after(
+                    lambda: flt.apply(f, p, g), lambda: flt.backward(f, p, G, g=g))
             out[f"stats_{spatial}"] = flt.stats()
             if bruteforce and spatial == "gauss":   # Eq. (1)-(2) on the same guide
                 gb = api.bruteforce(f, p, w["sigma_s"], w["sigma_r"])

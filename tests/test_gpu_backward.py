@@ -211,3 +211,39 @@ def test_autograd_with_live_sigmas(api):
     assert d0 > 0                                   # the loss grows with sigma_r above 0.2
     L1, _ = loss_and_grad(v - 0.1 * math.copysign(1.0, d0))
     assert L1 < L0
+
+
+def test_backward_after_apply_equals_the_recomputing_backward(api):
+    """hdf_backward_after_apply takes the range maps, coefficients,
+    denominators and guard list that the last apply left in the handle and
+    gives the gradients of hdf_backward bit for bit (no pixel here needs the
+    FP64 recomputation); it refuses when the handle's last call was not an
+    apply, and the autograd function uses it."""
+    f = synthetic.color_rectangles(70, 45, seed=97)
+    f = np.clip(f + np.random.default_rng(98).normal(0, 0.03, f.shape), 0, 1).astype(np.float32)
+    fd = torch.from_numpy(f).cuda()
+    G = torch.from_numpy(np.random.default_rng(99).normal(size=f.shape).astype(np.float32)).cuda()
+    flt = api.HDFilter(70, 45, 3, 3, 8, 2.0, 0.3)
+    flt.cluster(fd)
+    gf0, gs0, gr0 = flt.backward(fd, fd, G)
+    g = flt.apply(fd, fd)
+    gf1, gs1, gr1 = flt.backward(fd, fd, G, g=g)
+    assert torch.equal(gf0, gf1)
+    assert float(gs0) == float(gs1) and float(gr0) == float(gr1)
+    assert flt.stats()["rescued_pixels"] == 0
+    with pytest.raises(Exception):      # the backward ended the apply's state
+        flt.backward(fd, fd, G, g=g)
+    g = flt.apply(fd, fd)
+    flt.cluster(fd)
+    with pytest.raises(Exception):      # so does a clustering
+        flt.backward(fd, fd, G, g=g)
+    # autograd: forward then backward on the same handle takes the shortcut
+    fx = fd.clone().requires_grad_(True)
+    ls = torch.tensor(math.log(2.0), device="cuda", requires_grad=True)
+    lr = torch.tensor(math.log(0.3), device="cuda", requires_grad=True)
+    out = api.fast_filter(fx, ls, lr, flt)
+    seq = flt._seq
+    (out * G).sum().backward()
+    assert flt._seq == seq + 1
+    gf2, gs2, gr2 = flt.backward(fd, fd, G)
+    assert torch.equal(fx.grad, gf2)

@@ -102,6 +102,7 @@ typedef struct {
                             denominator sum_k c_k r_k was ill-conditioned (sum_k |c_k| r_k
                             above 64 times its magnitude) or within rounding of the guard's
                             threshold; counted in fallback_pixels when the FP64 guard fires */
+  int nlm_sweeps;        /* Jacobi sweeps of the last hdf_nlm_guide's eigendecomposition */
 } hdf_stats;
 
 /* Validate `desc`, fill in S if 0, and allocate the device workspace of one

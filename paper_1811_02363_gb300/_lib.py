@@ -26,7 +26,8 @@ class hdf_desc(C.Structure):
 class hdf_stats(C.Structure):
     _fields_ = [("K_eff", C.c_int), ("fallback_pixels", C.c_int), ("device_error", C.c_int),
                 ("lloyd_iters_max", C.c_int), ("rounds", C.c_int),
-                ("cluster_error", C.c_double), ("rescued_pixels", C.c_int)]
+                ("cluster_error", C.c_double), ("rescued_pixels", C.c_int),
+                ("nlm_sweeps", C.c_int)]
 
 
 HDF_BATCH_GRAPH, HDF_BATCH_TIMED, HDF_BATCH_SKIP_CLUSTER = 1, 2, 4

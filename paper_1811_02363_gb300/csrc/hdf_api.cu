@@ -375,6 +375,7 @@ hdf_status hdf_get_stats(hdf_handle* h, hdf_stats* out, void* stream) {
   out->device_error = c[hdf::CTRL_ERROR];
   out->fallback_pixels = c[hdf::CTRL_FALLBACK] + c[hdf::CTRL_FALLBACK64];
   out->rescued_pixels = c[hdf::CTRL_RESCUED];
+  out->nlm_sweeps = c[hdf::CTRL_NLM_SWEEPS];
   out->lloyd_iters_max = c[hdf::CTRL_LLOYD_MAX];
   out->rounds = c[hdf::CTRL_ROUNDS];
   out->cluster_error = ek;

@@ -825,6 +825,7 @@ hdf_status hdf_batch_get_stats(hdf_batch* b, int i, hdf_stats* out) {
   out->rounds = c[hdf::CTRL_ROUNDS];
   out->cluster_error = ek;
   out->rescued_pixels = 0;   // the batch keeps every pixel on the float32 path
+  out->nlm_sweeps = 0;
   return (hdf_status)c[hdf::CTRL_ERROR];
 }
 

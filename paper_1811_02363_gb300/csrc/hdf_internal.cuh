@@ -25,6 +25,7 @@ enum CtrlSlot {
   CTRL_FALLBACK64 = 7,   // of those, pixels that took the denominator guard
   CTRL_BARRIER = 8,      // grid barrier: arrival counter
   CTRL_BARRIER_GEN = 9,  // reserved (zeroed with the barrier counter)
+  CTRL_NLM_SWEEPS = 10,  // Jacobi sweeps of the last NLM guide
   CTRL_WORDS = 16
 };
 

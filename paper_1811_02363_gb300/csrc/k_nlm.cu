@@ -151,8 +151,267 @@ nlm_cov_kernel(const float* __restrict__ f, int n, int H, int W, int m, const do
   if (tid < D) out[NP + tid] = acc1;
 }
 
-// One CTA: the covariance in FP64 (sums of the blocks' float32 partials), its
-// eigendecomposition by cyclic Jacobi in float32, the top-rho basis.  The
+// The same per-block partials on the tensor cores (patch dimension D <= 64):
+// the block's pixels are taken in tiles of up to TC_KC pixels of one image
+// row; the tile's input rows (mirrored at the borders) are staged in shared
+// memory, loaded into registers during the previous tile; the tile's shifted
+// patch values x are split into a TF32 head and tail, x = h + l (h = x rounded to
+// TF32, l = x - h), and staged as a 128 x TC_KC operand whose rows 0..63 hold
+// h_a and rows 64..127 hold l_a (rows D..63 and 64 + D..127 zero).  One
+// tcgen05.mma chain per tile (kind::tf32, M = 128, N = 64, K = 8 pixels per
+// instruction) accumulates in tensor memory
+//   rows 0..63:   H_ab = sum_i h_a h_b,   rows 64..127: L_ab = sum_i l_a h_b,
+// and sum_i x_a x_b = H_ab + (L_ab + L_ba) up to the dropped sum_i l_a l_b
+// (relative 2^-22).  Operands in the no-swizzle K-major layout: 8-row x
+// 16-byte core matrices, K-adjacent ones 128 bytes apart, row-group-adjacent
+// ones TC_KC / 4 * 128 bytes apart.  Two operand buffers: the next tile is
+// staged while the tensor cores work on the current one.  Every wait is
+// bounded (the device status records HDF_ETIMEOUT).
+constexpr int TC_KC = 128;           // pixels per tile
+constexpr int TC_THREADS = 512;
+constexpr int TC_ROWS = 128;
+constexpr size_t TC_BUF_FLOATS = (size_t)TC_ROWS * TC_KC;
+
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  constexpr uint32_t LBO = 128, SBO = (TC_KC / 4) * 128;
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((LBO >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((SBO >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+__device__ __forceinline__ bool tc_wait(unsigned long long* mbar, unsigned parity,
+                                        unsigned long long limit_ns) {
+  const uint32_t m = (uint32_t)__cvta_generic_to_shared(mbar);
+  const uint64_t t0 = globaltimer_ns();
+  while (true) {
+    uint32_t done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(m), "r"(parity) : "memory");
+    if (done) return true;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
+  }
+}
+
+constexpr int TC_HALO = 2048;        // staged input floats per tile: n m (TC_KC + m - 1)
+constexpr int TC_HPT = TC_HALO / TC_THREADS;
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+nlm_cov_tc_kernel(const float* __restrict__ f, int n, int H, int W, int m, const double* mean_part,
+                  int nblk_mean, float* __restrict__ part, int* ctrl) {
+  extern __shared__ __align__(128) float tsm[];     // 2 operand buffers (then the epilogue), input rows
+  __shared__ uint32_t tmem_base;
+  __shared__ __align__(8) unsigned long long mbar[2];
+  __shared__ float shift[4];
+  __shared__ float fsum[TC_THREADS / 32][64];
+  __shared__ int roff[64];   // feature r -> offset of its (channel, dy, dx) in the staged rows
+  __shared__ int rch[64];    //            -> its channel
+  __shared__ int stop;
+  float* halo = tsm + 2 * TC_BUF_FLOATS;
+  const int D = n * m * m;
+  const int NP = D * (D + 1) / 2;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int hm = m / 2;
+  const int LDH = TC_KC + m - 1;                     // staged columns per input row
+  const int nhalo = n * m * LDH;                     // <= TC_HALO (checked by the launcher)
+  const int tpr = (W + TC_KC - 1) / TC_KC;           // tiles per image row
+  const int ntiles = H * tpr;
+  constexpr unsigned long long LIMIT = 2000000000ull;   // 2 s
+  if (tid < n) {
+    double t = 0.0;
+    for (int b = 0; b < nblk_mean; ++b) t += mean_part[(size_t)b * n + tid];
+    shift[tid] = (float)(t / ((double)H * W));
+  }
+  if (tid < 64) {
+    const int r = tid < D ? tid : 0;
+    const int c = r / (m * m), rr = r % (m * m);
+    roff[tid] = (c * m + rr / m) * LDH + rr % m;
+    rch[tid] = c;
+  }
+  for (size_t i = tid; i < 2 * TC_BUF_FLOATS; i += TC_THREADS) tsm[i] = 0.0f;
+  if (warp == 0) {
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&tmem_base);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(dst) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    stop = 0;
+    for (int b = 0; b < 2; ++b) {
+      const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar[b]);
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  // the input rows of tile t: value v = (channel, dy, column j) of the
+  // rows y - hm .. y + hm and columns x0 - hm .. x0 + TC_KC - 1 + hm, mirrored
+  auto load_halo = [&](int t, float (&hv)[TC_HPT]) {
+    const int y = t / tpr, x0 = (t % tpr) * TC_KC;
+#pragma unroll
+    for (int u = 0; u < TC_HPT; ++u) {
+      const int v = u * TC_THREADS + tid;
+      hv[u] = 0.0f;
+      if (t < ntiles && v < nhalo) {
+        const int j = v % LDH, cd = v / LDH, dy = cd % m, c = cd / m;
+        const int yy = mirror(y + dy - hm, H), xx = mirror(min(x0 + j - hm, W - 1 + hm), W);
+        hv[u] = __ldg(f + (size_t)c * H * W + (size_t)yy * W + xx);
+      }
+    }
+  };
+  // staging map: lane -> (row r & 7, column k & 3); a warp covers one
+  // 8 x 4 core matrix per step (conflict-free stores)
+  const int r8 = lane >> 2, k4 = lane & 3;
+  const int ngroups = (D + 7) / 8;
+  float fs[8];
+#pragma unroll
+  for (int g = 0; g < 8; ++g) fs[g] = 0.0f;
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | (8u << 17) | (8u << 24);
+  float hv[TC_HPT];
+  load_halo(blockIdx.x, hv);
+  int i = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+    const int b = i & 1;
+    float* buf = tsm + (size_t)b * TC_BUF_FLOATS;
+    const int cnt = min(TC_KC, W - (t % tpr) * TC_KC);   // pixels of this tile
+#pragma unroll
+    for (int u = 0; u < TC_HPT; ++u) {
+      const int v = u * TC_THREADS + tid;
+      if (v < nhalo) halo[v] = hv[u];
+    }
+    load_halo(t + gridDim.x, hv);   // the next tile's rows, in flight while this one is built
+    if (i >= 2) {   // the MMAs of tile i - 2 read this buffer
+      if (!tc_wait(&mbar[b], ((i - 2) >> 1) & 1, LIMIT) && tid == 0) stop = 1;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    __syncthreads();   // halo staged
+    // row group g (rows 8g + r8) of the operand: a warp fills the core
+    // matrices kq = warp, warp + 8, ... of each group
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      if (g >= ngroups) break;
+      const int r = 8 * g + r8;
+      const bool live = r < D;
+      const float* src = halo + (live ? roff[r] : 0);
+      const float sh = live ? shift[rch[r]] : 0.0f;
+      // float index of (row r, column k) of the operand:
+      // ((r / 8) (TC_KC / 4) + k / 4) 32 + (r % 8) 4 + k % 4
+      const int hi0 = ((g * (TC_KC / 4)) << 5) + (r8 << 2) + k4;         // (r, 4 kq + k4) - 32 kq
+      const int lo0 = (((8 + g) * (TC_KC / 4)) << 5) + (r8 << 2) + k4;   // the same for row 64 + r
+      float acc = 0.0f;
+#pragma unroll
+      for (int kq = warp; kq < TC_KC / 4; kq += TC_THREADS / 32) {
+        const int k = 4 * kq + k4;
+        const float x = (live && k < cnt) ? src[k] - sh : 0.0f;
+        acc += x;
+        const float h = to_tf32(x);
+        buf[hi0 + (kq << 5)] = h;
+        buf[lo0 + (kq << 5)] = x - h;
+      }
+      fs[g] += acc;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (stop) break;   // uniform
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t base = (uint32_t)__cvta_generic_to_shared(buf);
+      for (int j = 0; j < TC_KC / 8; ++j) {
+        const uint64_t d = tc_desc(base + j * 256);   // 8 pixels = two core matrices along K
+        const uint32_t acc = (i > 0 || j > 0) ? 1u : 0u;
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                     " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                     ::"r"(tmem), "l"(d), "l"(d), "r"(idesc), "r"(acc) : "memory");
+      }
+      const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar[b]);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   ::"r"(mb) : "memory");
+    }
+  }
+  const int nmine = i;
+  // the last commit covers every MMA issued before it
+  bool ok = !stop;
+  if (nmine > 0) {
+    const int L = nmine - 1;
+    if (!tc_wait(&mbar[L & 1], (L >> 1) & 1, LIMIT)) ok = false;
+    if (!ok) tc_wait(&mbar[L & 1], (L >> 1) & 1, LIMIT);   // let the MMAs land before leaving
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) record_error(ctrl, HDF_ETIMEOUT);
+  } else {
+    // feature sums: lanes with the same row (r8) and group, then warps, in a fixed order
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      float v = fs[g];
+      v += __shfl_xor_sync(0xffffffffu, v, 1);
+      v += __shfl_xor_sync(0xffffffffu, v, 2);
+      if (k4 == 0) fsum[warp][8 * g + r8] = v;
+    }
+    float* ep = tsm;   // [128][65] accumulator rows
+    if (warp < 4) {
+      for (int half = 0; half < 2; ++half) {
+        uint32_t v[32];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(half * 32);
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                     "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                       "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+                       "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+                       "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                     : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int row = warp * 32 + lane;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) ep[row * 65 + half * 32 + c] = nmine > 0 ? __uint_as_float(v[c]) : 0.0f;
+      }
+    }
+    __syncthreads();
+    float* out = part + (size_t)blockIdx.x * (NP + D);
+    for (int v = tid; v < D * D; v += TC_THREADS) {
+      const int a = v / D, bb = v % D;
+      if (a > bb) continue;
+      out[a * D - a * (a - 1) / 2 + (bb - a)] = ep[a * 65 + bb] + (ep[(64 + a) * 65 + bb] + ep[(64 + bb) * 65 + a]);
+    }
+    if (tid < D) {
+      float t = 0.0f;
+      for (int w = 0; w < TC_THREADS / 32; ++w) t += fsum[w][tid];
+      out[NP + tid] = t;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
+}
+
+// FP64 sums over the blocks of their partials, one thread per entry (pair
+// sums and feature sums), the blocks in ascending order.
+__global__ void __launch_bounds__(128)
+nlm_sum_kernel(const float* __restrict__ part, int nblk, int len, double* __restrict__ sum) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= len) return;
+  double t = 0.0;
+  int b = 0;
+  for (; b + 8 <= nblk; b += 8) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = __ldg(part + (size_t)(b + u) * len + q);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) t += (double)v[u];
+  }
+  for (; b < nblk; ++b) t += (double)__ldg(part + (size_t)b * len + q);
+  sum[q] = t;
+}
+
+// One CTA: the covariance in FP64 (from the FP64 sums of the blocks' float32
+// partials), its eigendecomposition by cyclic Jacobi in float32, the top-rho
+// basis.  The
 // blocks' partial sums are float32 sums over some 7000 pixels each, so the
 // covariance carries a relative rounding of order 1e-6; float32 rotations
 // (1e-7) add nothing of consequence, and on this GPU they run at the FP32
@@ -163,7 +422,7 @@ nlm_cov_kernel(const float* __restrict__ f, int n, int H, int W, int m, const do
 // a sweep no longer halves that norm (Jacobi converges quadratically until
 // rounding noise is all that is left).
 __global__ void __launch_bounds__(NL_THREADS)
-nlm_eig_kernel(const float* __restrict__ part, int nblk, int n, int m, int N, int rho,
+nlm_eig_kernel(const double* __restrict__ csum, int n, int m, int N, int rho,
                const double* mean_part, int nblk_mean, float* __restrict__ basis,
                float* __restrict__ pmean, int* ctrl) {
   extern __shared__ double dm[];
@@ -177,16 +436,13 @@ nlm_eig_kernel(const float* __restrict__ part, int nblk, int n, int m, int N, in
   __shared__ double shift[4];
   __shared__ int rotated;
   const int tid = threadIdx.x;
+  if (tid == 0 && ctrl) ctrl[CTRL_NLM_SWEEPS] = 0;
   if (tid < n) {
     double t = 0.0;
     for (int b = 0; b < nblk_mean; ++b) t += mean_part[(size_t)b * n + tid];
     shift[tid] = (double)(float)(t / (double)N);    // the float shift the covariance pass used
   }
-  for (int a = tid; a < D; a += NL_THREADS) {
-    double t = 0.0;
-    for (int b = 0; b < nblk; ++b) t += (double)part[(size_t)b * (NP + D) + NP + a];
-    mu[a] = t / (double)N;
-  }
+  for (int a = tid; a < D; a += NL_THREADS) mu[a] = csum[NP + a] / (double)N;
   __syncthreads();
   for (int idx = tid; idx < DE * DE; idx += NL_THREADS) {
     const int i = idx / DE, j = idx % DE;
@@ -194,9 +450,7 @@ nlm_eig_kernel(const float* __restrict__ part, int nblk, int n, int m, int N, in
     if (i < D && j < D) {
       const int a = i < j ? i : j, b = i < j ? j : i;
       const int q = a * D - a * (a - 1) / 2 + (b - a);  // pair index of (a, b)
-      double t = 0.0;
-      for (int bl = 0; bl < nblk; ++bl) t += (double)part[(size_t)bl * (NP + D) + q];
-      v = t / (double)N - mu[a] * mu[b];
+      v = csum[q] / (double)N - mu[a] * mu[b];
     }
     A[idx] = (float)v;
     V[idx] = (i == j) ? 1.0f : 0.0f;
@@ -289,6 +543,7 @@ nlm_eig_kernel(const float* __restrict__ part, int nblk, int n, int m, int N, in
     }
     const int any = rotated;   // read after the barrier that ended the sweep's last step
     __syncthreads();           // everyone has read it before thread 0 resets it
+    if (tid == 0 && ctrl) ctrl[CTRL_NLM_SWEEPS] = sweep + 1;
     if (!any) break;
   }
   // the rho largest eigenvalues (ties -> lower index); basis[d][a], mean patch
@@ -309,7 +564,6 @@ nlm_eig_kernel(const float* __restrict__ part, int nblk, int n, int m, int N, in
     basis[idx] = V[a * DE + pp[d]];
   }
   for (int a = tid; a < D; a += NL_THREADS) pmean[a] = (float)(mu[a] + shift[a / (m * m)]);
-  (void)ctrl;
 }
 
 template <int RMAX>
@@ -347,7 +601,7 @@ nlm_project_kernel(const float* __restrict__ f, int n, int H, int W, int m, int 
 size_t nlm_workspace_bytes(int G) {
   const int D = NL_MAXD;
   return sizeof(float) * (size_t)G * (D * (D + 1) / 2 + D) + sizeof(double) * (size_t)G * 4 +
-         sizeof(float) * (D * HDF_MAX_RHO + D) + 1024;
+         sizeof(float) * (D * HDF_MAX_RHO + D) + sizeof(double) * (D * (D + 1) / 2 + D) + 1024;
 }
 
 cudaError_t launch_nlm_guide(const float* f, int n, int H, int W, int m, int rho, float* p,
@@ -365,23 +619,34 @@ cudaError_t launch_nlm_guide(const float* f, int n, int H, int W, int m, int rho
   unsigned char* w = (unsigned char*)ws;
   float* cov_part = (float*)w;
   double* mean_part = (double*)(w + sizeof(float) * (size_t)G * (NP + D) + 64 - ((sizeof(float) * (size_t)G * (NP + D)) & 63));
-  float* basis = (float*)(mean_part + (size_t)G * 4);
+  double* cov_sum = mean_part + (size_t)G * 4;       // NP + D
+  float* basis = (float*)(cov_sum + NP + D);
   float* pmean = basis + rho * D;
   const int N = H * W;
   nlm_mean_kernel<<<G, NL_THREADS, 0, st>>>(f, n, N, mean_part);
-  const int DP = (D + 3) & ~3, NBR = DP / 4, NB = NBR * (NBR + 1) / 2;
-  const int NPAR = NB <= NL_THREADS ? NL_THREADS / NB : 1;
-  const size_t smem_cov =
-      sizeof(float) * ((size_t)(DP | 1) * NL_TILE * NL_TILE + (size_t)NPAR * NB * 16);
-  cudaError_t e = cudaFuncSetAttribute(nlm_cov_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_cov);
-  if (e != cudaSuccess) return e;
-  nlm_cov_kernel<<<G, NL_THREADS, smem_cov, st>>>(f, n, H, W, m, mean_part, G, cov_part);
+  cudaError_t e;
+  if (D <= 64 && n * m * (TC_KC + m - 1) <= TC_HALO) {   // tensor cores
+    const size_t smem_tc = sizeof(float) * (2 * TC_BUF_FLOATS + TC_HALO);
+    e = cudaFuncSetAttribute(nlm_cov_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_tc);
+    if (e != cudaSuccess) return e;
+    nlm_cov_tc_kernel<<<G, TC_THREADS, smem_tc, st>>>(f, n, H, W, m, mean_part, G, cov_part, ctrl);
+  } else {
+    const int DP = (D + 3) & ~3, NBR = DP / 4, NB = NBR * (NBR + 1) / 2;
+    const int NPAR = NB <= NL_THREADS ? NL_THREADS / NB : 1;
+    const size_t smem_cov =
+        sizeof(float) * ((size_t)(DP | 1) * NL_TILE * NL_TILE + (size_t)NPAR * NB * 16);
+    e = cudaFuncSetAttribute(nlm_cov_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_cov);
+    if (e != cudaSuccess) return e;
+    nlm_cov_kernel<<<G, NL_THREADS, smem_cov, st>>>(f, n, H, W, m, mean_part, G, cov_part);
+  }
   const int DE = D + (D & 1);
   const size_t smem_eig = sizeof(double) * (size_t)(D + (D & 1)) + sizeof(float) * 2 * (size_t)DE * DE;
   e = cudaFuncSetAttribute(nlm_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_eig);
   if (e != cudaSuccess) return e;
-  nlm_eig_kernel<<<1, NL_THREADS, smem_eig, st>>>(cov_part, G, n, m, N, rho, mean_part, G, basis,
+  nlm_sum_kernel<<<(NP + D + 127) / 128, 128, 0, st>>>(cov_part, G, NP + D, cov_sum);
+  nlm_eig_kernel<<<1, NL_THREADS, smem_eig, st>>>(cov_sum, n, m, N, rho, mean_part, G, basis,
                                                   pmean, ctrl);
   const size_t smem_p = sizeof(float) * ((size_t)rho * D + D);
   if (rho <= 8)

@@ -117,12 +117,11 @@ hdf_status hdf_create(hdf_handle** out, const hdf_desc* desc);
 /* Release everything hdf_create allocated.  Synchronises the device. */
 void hdf_destroy(hdf_handle* h);
 
-/* Limit of each device-side wait of hdf_cluster (its grid barriers, the wait
- * of a split's finishing block for the other blocks' partial sums, and the
- * completion of its bulk copies), in seconds, 0..60; the default is 2 s.  A
- * wait that reaches the limit records HDF_ETIMEOUT in the device status word
- * and every block of the launch returns (after its own copies in flight have
- * landed); hdf_get_stats then reports HDF_ETIMEOUT and the centres are not
+/* Limit of each device-side wait of hdf_cluster (its grid barriers and the
+ * wait of a split's finishing block for the other blocks' partial sums), in
+ * seconds, 0..60; the default is 2 s.  A wait that reaches the limit records
+ * HDF_ETIMEOUT in the device status word and every block of the launch
+ * returns; hdf_get_stats then reports HDF_ETIMEOUT and the centres are not
  * valid.  For failure handling and its tests; not part of the paper's method.
  * Errors: HDF_EINVAL (NULL handle, limit outside 0..60). */
 hdf_status hdf_set_wait_limit(hdf_handle* h, double seconds);

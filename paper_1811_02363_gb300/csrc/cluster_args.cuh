@@ -87,7 +87,7 @@ struct ClArgs {
 };
 
 // Floats per partial record of a block: rho double-float pairs and one more
-// pair, padded to 16 bytes (records are fetched by bulk copies).
+// pair, padded to 16 bytes (records are fetched in 16-byte words).
 __host__ __device__ constexpr int record_floats(int rho) { return ((2 * (rho + 1) + 3) / 4) * 4; }
 
 // Host helpers (k_cluster.cu).

@@ -109,8 +109,6 @@ struct ClShared {
   int ok;
   int all_done;
   int tr_n;              // trace events recorded (block 0)
-  unsigned long long mbar;   // completion barrier of the record bulk copies
-  unsigned mb_phase;         // its current phase parity
   float bmax;            // block maximum of the last block_max_sum
   int last;              // this block is the last contributor of a split
 };
@@ -134,42 +132,6 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
-}
-
-// Bulk copy (async proxy) global -> shared, completion counted in bytes on
-// an mbarrier.  Addresses and size multiples of 16 bytes.
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes,
-                                              unsigned long long* mbar) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  const unsigned m = (unsigned)__cvta_generic_to_shared(mbar);
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-               ::"r"(d), "l"(src), "r"(bytes), "r"(m) : "memory");
-}
-__device__ __forceinline__ void mbar_init(unsigned long long* mbar, unsigned count) {
-  const unsigned m = (unsigned)__cvta_generic_to_shared(mbar);
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(m), "r"(count) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* mbar, unsigned bytes) {
-  const unsigned m = (unsigned)__cvta_generic_to_shared(mbar);
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(m), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async;" ::: "memory");
-}
-// Wait for the phase of the given parity to complete; false after limit_ns.
-__device__ __forceinline__ int mbar_wait(unsigned long long* mbar, unsigned parity,
-                                         unsigned long long limit_ns) {
-  const unsigned m = (unsigned)__cvta_generic_to_shared(mbar);
-  const unsigned long long t0 = globaltimer_ns();
-  while (true) {
-    unsigned done;
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                 " selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(m), "r"(parity) : "memory");
-    if (done) return 1;
-    if (globaltimer_ns() - t0 > limit_ns) return 0;
-  }
 }
 
 __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
@@ -1104,40 +1066,21 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
       __syncthreads();
       return s.last != 0;
     };
-    // Bulk copies of the nc partial records of split i (record of contributor
-    // c at block contrib_block(c)) into dst, completed on the block's mbarrier;
-    // bounded wait.  False (device status set) if the copies did not land.
-    auto stage_records = [&](int i, int it, int nc, float* dst) -> bool {
-      const unsigned bytes = (unsigned)(PS * sizeof(float));
-      if (tid == 0) {
-        fence_proxy_async();   // earlier generic accesses before the async writes
-        mbar_expect_tx(&s.mbar, bytes * (unsigned)nc);
+    // The nc partial records of split i (record of contributor c at block
+    // contrib_block(c)) into dst: 16-byte loads spread over the block, all in
+    // flight at once.  Thread 0's acquire of the arrival count and the block
+    // barrier after it make the records visible.
+    auto stage_records = [&](int i, int it, int nc, float* dst) {
+      const float* lpf = a.pf + (1 + (it & 1)) * pf_stride;
+      const int Q = PS / 4;   // 16-byte words per record
+      for (int v = tid; v < nc * Q; v += CL_THREADS) {
+        const int c = v / Q, w = v - c * Q;
+        const float4 x = __ldcg(reinterpret_cast<const float4*>(
+                                    lpf + ((size_t)contrib_block(a, s, i, c) * MAXSEG + i) * PS) + w);
+        reinterpret_cast<float4*>(dst + (size_t)c * PS)[w] = x;
       }
       __syncthreads();
-      for (int c = tid; c < nc; c += CL_THREADS) {
-        const size_t off = (size_t)contrib_block(a, s, i, c) * MAXSEG + i;
-        bulk_copy_g2s(dst + (size_t)c * PS, a.pf + (1 + (it & 1)) * pf_stride + off * PS, bytes,
-                      &s.mbar);
-      }
-      if (tid == 0) {
-        int ok = mbar_wait(&s.mbar, s.mb_phase, a.wait_ns);
-        if (!ok) {
-          record_error(a.ctrl, HDF_ETIMEOUT);
-          // let the copies in flight land before the block can leave (the
-          // default limit, however short the configured one is)
-          mbar_wait(&s.mbar, s.mb_phase, DEFAULT_WAIT_NS);
-        }
-        s.mb_phase ^= 1u;
-        s.last = ok;
-      }
-      __syncthreads();
-      return s.last != 0;
     };
-    // Lloyd update of split i by its finishing block: reduce the
-    // partial records in a fixed order (warp per value, lanes over the
-    // contributors, xor tree), decide the split's state, compute the new
-    // centres (means of the two sides) and the distance they moved, and
-    // publish all of it for the other blocks (read after the grid barrier).
     // Lloyd update of split i from its reduced sums fin = tmp + i (rho + 2),
     // by one warp (lanes over the coordinates): accept, revert or stop, the
     // new FP64 centres and the movement bounds behind the skip test, then
@@ -1230,11 +1173,11 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
     auto finish_split = [&](int i, int it) -> bool {
       const int nc = contrib_count(a, s, i);
       const int V = rho + 2;
-      // Fetch the nc records into shared memory with bulk copies (all in
-      // flight at once), then reduce them in a fixed order: thread (g, v)
+      // Fetch the nc records into shared memory, then reduce them in a
+      // fixed order: thread (g, v)
       // sums value v of the records c = g, g + NG, ... (ascending), and
       // fin[v] = ((part_0 + part_1) + ...) + part_{NG-1}.
-      if (!stage_records(i, it, nc, red)) return false;
+      stage_records(i, it, nc, red);
       const int VS = V <= 32 ? 32 : (V <= 64 ? 64 : 128);   // value slots
       const int NG = CL_THREADS / VS;                        // record classes
       {
@@ -1821,8 +1764,6 @@ cluster_kernel(const ClArgs* __restrict__ table, const int4* __restrict__ groups
   __shared__ int4 s_grp;
   extern __shared__ __align__(128) unsigned char dyn[];
   if (threadIdx.x == 0) {
-    mbar_init(&s.mbar, 1);
-    s.mb_phase = 0;
     s_grp = make_int4(0, 0, 0, 0);
     for (int g = 0; g < ngroups; ++g) {
       const int4 gr = groups[g];

@@ -30,7 +30,7 @@ enum CtrlSlot {
 };
 
 // Default limit of every device-side wait (grid barriers, split finishers,
-// bulk-copy completion) before the kernel records HDF_ETIMEOUT and returns.
+// tensor-core completion) before the kernel records HDF_ETIMEOUT and returns.
 constexpr unsigned long long kDefaultWaitNs = 2000000000ull;
 
 // Record `code` as the device error unless one is already recorded.

@@ -120,31 +120,46 @@ bwd_final_kernel(const float* __restrict__ f, const GT* __restrict__ p, int guid
       gacc[d] = 0.0f;
     }
     float t = 0.0f;
+    // centres in groups of KC: their b_k and beta_k loaded together first
+    // (up to 16 centres; beyond, the registers this takes cost more
+    // occupancy than the loads in flight gain)
+    constexpr int KC = KMAX <= 16 ? 8 : 1;
 #pragma unroll 1
-    for (int k = 0; k < K; ++k) {
-      float eta = 0.0f, dAc = 0.0f;
-      if (!fb) {
+    for (int k0 = 0; k0 < K; k0 += KC) {
+      float bkv[KC], btv[KC];
 #pragma unroll
-        for (int l = 0; l < KMAX; ++l) {
-          if (l < K) {
-            eta = fmaf(spi[k * K + l], gv[l], eta);
-            dAc = fmaf(sdA[k * K + l], cv[l], dAc);
+      for (int j = 0; j < KC; ++j) {
+        const int k = k0 + j;
+        bkv[j] = k < K ? B[(size_t)k * N + pix] : 0.0f;
+        btv[j] = k < K ? bet[(size_t)k * N + pix] : 0.0f;
+      }
+#pragma unroll
+      for (int j = 0; j < KC; ++j) {
+        const int k = k0 + j;
+        if (k >= K) break;
+        float eta = 0.0f, dAc = 0.0f;
+        if (!fb) {
+#pragma unroll
+          for (int l = 0; l < KMAX; ++l) {
+            if (l < K) {
+              eta = fmaf(spi[k * K + l], gv[l], eta);
+              dAc = fmaf(sdA[k * K + l], cv[l], dAc);
+            }
           }
         }
-      }
-      const float bk = B[(size_t)k * N + pix];
-      const float beta = bet[(size_t)k * N + pix] + eta;          // dL/db_k
-      const float coef = beta * bk * inv_sr2;
-      float d2 = 0.0f;
+        const float beta = btv[j] + eta;                              // dL/db_k
+        const float coef = beta * bkv[j] * inv_sr2;
+        float d2 = 0.0f;
 #pragma unroll
-      for (int d = 0; d < RMAX; ++d) {
-        if (d < rho) {
-          const float dd = smu[k * rho + d] - x[d];
-          d2 = fmaf(dd, dd, d2);
-          gacc[d] = fmaf(coef, dd, gacc[d]);                       // b_k (mu_k - p) / sigma_r^2
+        for (int d = 0; d < RMAX; ++d) {
+          if (d < rho) {
+            const float dd = smu[k * rho + d] - x[d];
+            d2 = fmaf(dd, dd, d2);
+            gacc[d] = fmaf(coef, dd, gacc[d]);                       // b_k (mu_k - p) / sigma_r^2
+          }
         }
+        t += coef * d2 - eta * dAc;
       }
-      t += coef * d2 - eta * dAc;
     }
     acc += (double)t;
     if (guide_is_image) {

@@ -500,10 +500,13 @@ nlm_eig_kernel(const double* __restrict__ csum, int n, int m, int N, int rho,
         float c = 1.0f, sn = 0.0f;
         const float apq = A[p * DE + q];
         const float app = A[p * DE + p], aqq = A[q * DE + q];
-        if (fabsf(apq) > 1.1920929e-7f * sqrtf(fabsf(app * aqq)) && apq != 0.0f) {
-          const float tau = (aqq - app) / (2.0f * apq);
-          const float t = tau >= 0.0f ? 1.0f / (tau + sqrtf(1.0f + tau * tau))
-                                      : -1.0f / (-tau + sqrtf(1.0f + tau * tau));
+        // |a_pq| > 2^-23 sqrt(|a_pp a_qq|), squared; then the smaller root t
+        // of t^2 + 2 theta t - 1 = 0, theta = (a_qq - a_pp) / (2 a_pq), as
+        // sgn(d) e / (|d| + sqrt(d^2 + e^2)) with d = a_qq - a_pp, e = 2 a_pq
+        // (one square root and one division on the round's serial path)
+        if (apq * apq > 1.4210855e-14f * fabsf(app * aqq) && apq != 0.0f) {
+          const float d = aqq - app, e = 2.0f * apq;
+          const float t = (d >= 0.0f ? e : -e) / (fabsf(d) + sqrtf(d * d + e * e));
           c = 1.0f / sqrtf(1.0f + t * t);
           sn = t * c;
           rotated = 1;

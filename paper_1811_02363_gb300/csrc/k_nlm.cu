@@ -569,29 +569,65 @@ nlm_eig_kernel(const double* __restrict__ csum, int n, int m, int N, int rho,
   for (int a = tid; a < D; a += NL_THREADS) pmean[a] = (float)(mu[a] + shift[a / (m * m)]);
 }
 
+// Projection of every pixel's shifted patch on the rho leading eigenvectors.
+// Per patch coordinate a the block keeps its offset from the pixel (for
+// pixels at least m / 2 from every border, one load per coordinate) and its
+// (channel, dy, dx) for the mirrored border pixels.
 template <int RMAX>
 __global__ void __launch_bounds__(NL_THREADS)
 nlm_project_kernel(const float* __restrict__ f, int n, int H, int W, int m, int rho,
                    const float* __restrict__ basis, const float* __restrict__ pmean,
                    float* __restrict__ p) {
   extern __shared__ float sb[];
-  const int D = n * m * m;
+  const int D = n * m * m, hm = m / 2;
+  const size_t N = (size_t)H * W;
   float* sbasis = sb;                // rho x D
   float* smean = sb + rho * D;       // D
+  long long* soff = reinterpret_cast<long long*>(smean + D + ((rho * D + D) & 1));   // D
+  int* sdy = reinterpret_cast<int*>(soff + D);                                        // D
+  int* sdx = sdy + D;
+  int* sch = sdx + D;
+  float* sbt = reinterpret_cast<float*>(sch + D + (((size_t)(sch + D) & 15) ? (16 - ((size_t)(sch + D) & 15)) / 4 : 0));   // D x 8
   for (int i = threadIdx.x; i < rho * D; i += blockDim.x) sbasis[i] = basis[i];
-  for (int i = threadIdx.x; i < D; i += blockDim.x) smean[i] = pmean[i];
+  if (RMAX <= 8)
+    for (int i = threadIdx.x; i < 8 * D; i += blockDim.x) {
+      const int a = i / 8, d = i % 8;
+      sbt[i] = d < rho ? basis[d * D + a] : 0.0f;
+    }
+  for (int a = threadIdx.x; a < D; a += blockDim.x) {
+    smean[a] = pmean[a];
+    const int c = a / (m * m), r = a % (m * m);
+    sdy[a] = r / m - hm;
+    sdx[a] = r % m - hm;
+    sch[a] = c;
+    soff[a] = (long long)c * (long long)N + (long long)sdy[a] * W + sdx[a];
+  }
   __syncthreads();
-  const size_t N = (size_t)H * W;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (int)N; i += gridDim.x * blockDim.x) {
     const int y = i / W, x = i % W;
     float acc[RMAX];
 #pragma unroll
     for (int d = 0; d < RMAX; ++d) acc[d] = 0.0f;
-    for (int a = 0; a < D; ++a) {
-      const float v = patch_val(f, H, W, m, a, y, x) - smean[a];
+    if (RMAX <= 8 && y >= hm && y < H - hm && x >= hm && x < W - hm) {
+      // basis rows of coordinate a as two 16-byte words (coordinate-major copy)
+      const float4* bt = reinterpret_cast<const float4*>(sbt);
+      const float* fp = f + i;
+#pragma unroll 7
+      for (int a = 0; a < D; ++a) {
+        const float v = __ldg(fp + soff[a]) - smean[a];
+        const float4 b0 = bt[2 * a], b1 = bt[2 * a + 1];
+        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-      for (int d = 0; d < RMAX; ++d)
-        if (d < rho) acc[d] = fmaf(sbasis[d * D + a], v, acc[d]);
+        for (int d = 0; d < (RMAX < 8 ? RMAX : 8); ++d) acc[d] = fmaf(bv[d], v, acc[d]);
+      }
+    } else {
+      for (int a = 0; a < D; ++a) {
+        const int yy = mirror(y + sdy[a], H), xx = mirror(x + sdx[a], W);
+        const float v = __ldg(f + (size_t)sch[a] * N + (size_t)yy * W + xx) - smean[a];
+#pragma unroll
+        for (int d = 0; d < RMAX; ++d)
+          if (d < rho) acc[d] = fmaf(sbasis[d * D + a], v, acc[d]);
+      }
     }
 #pragma unroll
     for (int d = 0; d < RMAX; ++d)
@@ -651,7 +687,8 @@ cudaError_t launch_nlm_guide(const float* f, int n, int H, int W, int m, int rho
   nlm_sum_kernel<<<(NP + D + 127) / 128, 128, 0, st>>>(cov_part, G, NP + D, cov_sum);
   nlm_eig_kernel<<<1, NL_THREADS, smem_eig, st>>>(cov_sum, n, m, N, rho, mean_part, G, basis,
                                                   pmean, ctrl);
-  const size_t smem_p = sizeof(float) * ((size_t)rho * D + D);
+  const size_t smem_p = sizeof(float) * ((size_t)rho * D + D + 1) + (sizeof(long long) + 3 * sizeof(int)) * (size_t)D +
+                        16 + sizeof(float) * 8 * (size_t)D;
   if (rho <= 8)
     nlm_project_kernel<8><<<G * 4, NL_THREADS, smem_p, st>>>(f, n, H, W, m, rho, basis, pmean, p);
   else

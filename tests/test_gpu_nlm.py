@@ -1,11 +1,12 @@
 """GPU guide for nonlocal means (7x7 patches reduced by PCA) against the FP64
 oracle.  Eigenvector signs are arbitrary, so each feature plane is compared
 up to sign, at max-abs <= 1e-4 (the float32 tolerance of the other parity
-tests).  The covariance is accumulated in float32 per block and FP64 across
-blocks, and diagonalised by float32 Jacobi rotations; an eigenvector's error
-grows like the covariance's relative rounding over its eigen-gap, and the
-cases here keep it below 2e-5 down to gaps of 6e-5 of the largest
-eigenvalue."""
+tests).  The covariance is accumulated per block (on the tensor cores with a
+TF32 head/tail split for patch dimensions up to 64, in float32 FMAs beyond)
+and in FP64 across blocks, and diagonalised by float32 Jacobi rotations; an
+eigenvector's error grows like the covariance's relative rounding over its
+eigen-gap, and the cases here keep it below 4e-5 down to gaps of 6e-5 of the
+largest eigenvalue."""
 import numpy as np
 import pytest
 import torch
@@ -55,3 +56,22 @@ def test_nlm_pipeline_on_the_gpu_guide(api):
     assert np.all(np.isfinite(g))
     # with non-negative weights the output of the guard-free pixels stays close to the data range
     assert g.min() > f.min() - 0.1 and g.max() < f.max() + 0.1
+
+
+@pytest.mark.parametrize("H,W,n,patch,dims", [(90, 84, 1, 9, 6), (88, 70, 2, 5, 5)])
+def test_nlm_guide_other_patch_dimensions(api, H, W, n, patch, dims):
+    """9x9 patches of one channel (81 dimensions: the FMA covariance) and 5x5
+    patches of two channels (50 dimensions: the tensor-core covariance with
+    two channels' rows staged per tile)."""
+    f = np.concatenate([synthetic.smooth_field_with_edges(H, W, seed=H + W + c) for c in range(n)])
+    f = np.ascontiguousarray(f.astype(np.float32))
+    ref, basis, lam = O.pca_guide(f.astype(np.float64), patch, dims)
+    assert np.all(np.diff(lam[:dims + 1]) < 0)
+    flt = api.HDFilter(H, W, n, dims, 8, 5.0, 0.15)
+    p = flt.nlm_guide(torch.from_numpy(f).cuda(), patch).cpu().numpy()
+    for d in range(dims):
+        sgn = 1.0 if float((p[d] * ref[d]).sum()) >= 0 else -1.0
+        err = np.max(np.abs(sgn * p[d] - ref[d]))
+        gap = (lam[d] - lam[d + 1]) / lam[0]
+        print(f"{H}x{W}x{n} patch {patch} feature {d}: max-abs {err:.2e}, eigen-gap {gap:.2e}")
+        assert err <= 1e-4, (d, err)

@@ -1073,11 +1073,28 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
     auto stage_records = [&](int i, int it, int nc, float* dst) {
       const float* lpf = a.pf + (1 + (it & 1)) * pf_stride;
       const int Q = PS / 4;   // 16-byte words per record
-      for (int v = tid; v < nc * Q; v += CL_THREADS) {
-        const int c = v / Q, w = v - c * Q;
-        const float4 x = __ldcg(reinterpret_cast<const float4*>(
-                                    lpf + ((size_t)contrib_block(a, s, i, c) * MAXSEG + i) * PS) + w);
-        reinterpret_cast<float4*>(dst + (size_t)c * PS)[w] = x;
+      // words per thread in flight together: the long records of guides of
+      // 16 or more dimensions need several per thread
+      constexpr int U = RMAX >= 16 ? 8 : 1;
+      for (int v0 = tid; v0 < nc * Q; v0 += U * CL_THREADS) {
+        float4 x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int v = v0 + u * CL_THREADS;
+          if (v < nc * Q) {
+            const int c = v / Q, w = v - c * Q;
+            x[u] = __ldcg(reinterpret_cast<const float4*>(
+                              lpf + ((size_t)contrib_block(a, s, i, c) * MAXSEG + i) * PS) + w);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int v = v0 + u * CL_THREADS;
+          if (v < nc * Q) {
+            const int c = v / Q, w = v - c * Q;
+            reinterpret_cast<float4*>(dst + (size_t)c * PS)[w] = x[u];
+          }
+        }
       }
       __syncthreads();
     };

@@ -293,9 +293,11 @@ filter_tile_kernel(const FilterArgs a, const Taps taps) {
     // ---- row pass over every halo row: H = omega_1 (*) (b_k f).  Tasks of
     // XH outputs fill whole rounds of the block; the remainder is split into
     // tasks of XH / 2 outputs, so that the last round keeps every thread busy.
+    // When all tasks fit in one round they stay whole (halves would take two
+    // rounds and load each input window twice as often per output).
     {
       constexpr int T = P * HR * NSEG;
-      constexpr int FULL = (T / NT) * NT;
+      constexpr int FULL = T <= NT ? T : (T / NT) * NT;
       auto task_rows = [&](int task, int& q, int& r, int& seg) {
         q = task / (HR * NSEG);
         const int rem = task - q * (HR * NSEG);

@@ -144,10 +144,11 @@ __device__ __forceinline__ void batch_tile_item(const BatchImg* __restrict__ imp
                                                 : 0.0f;
     }
     // row pass over every halo row of every plane of the chunk; the rounds
-    // that do not fill the block run tasks of XH / 2 outputs
+    // that do not fill the block run tasks of XH / 2 outputs, unless all
+    // tasks fit in one round (then they stay whole)
     {
       const int T = P * HR * NSEG;
-      const int FULL = (T / NT) * NT;
+      const int FULL = T <= NT ? T : (T / NT) * NT;
       auto tap = [&](int t) { return wh[t <= SB ? t : 2 * SB - t]; };
       auto task_rows = [&](int task, int& q, int& r, int& seg) {
         q = task / (HR * NSEG);

@@ -19,6 +19,7 @@ namespace {
 constexpr int NL_THREADS = 256;
 constexpr int NL_TILE = 16;          // pixels per tile side in the covariance pass
 constexpr int NL_MAXD = 96;          // patch dimension n * patch^2 handled by the FP64 eigen step
+constexpr int EIG_THREADS = 1024;    // the one-CTA eigendecomposition: short row loops per round
 
 __device__ __forceinline__ int mirror(int i, int n) {
   // reflect without repeating the edge: -1 -> 1, n -> n - 2 (n >= 2)
@@ -421,7 +422,7 @@ nlm_sum_kernel(const float* __restrict__ part, int nblk, int len, double* __rest
 // rotations, at the float32 rounding level of the off-diagonal norm, or when
 // a sweep no longer halves that norm (Jacobi converges quadratically until
 // rounding noise is all that is left).
-__global__ void __launch_bounds__(NL_THREADS)
+__global__ void __launch_bounds__(EIG_THREADS)
 nlm_eig_kernel(const double* __restrict__ csum, int n, int m, int N, int rho,
                const double* mean_part, int nblk_mean, float* __restrict__ basis,
                float* __restrict__ pmean, int* ctrl) {
@@ -442,9 +443,9 @@ nlm_eig_kernel(const double* __restrict__ csum, int n, int m, int N, int rho,
     for (int b = 0; b < nblk_mean; ++b) t += mean_part[(size_t)b * n + tid];
     shift[tid] = (double)(float)(t / (double)N);    // the float shift the covariance pass used
   }
-  for (int a = tid; a < D; a += NL_THREADS) mu[a] = csum[NP + a] / (double)N;
+  for (int a = tid; a < D; a += EIG_THREADS) mu[a] = csum[NP + a] / (double)N;
   __syncthreads();
-  for (int idx = tid; idx < DE * DE; idx += NL_THREADS) {
+  for (int idx = tid; idx < DE * DE; idx += EIG_THREADS) {
     const int i = idx / DE, j = idx % DE;
     double v = 0.0;
     if (i < D && j < D) {
@@ -457,20 +458,20 @@ nlm_eig_kernel(const double* __restrict__ csum, int n, int m, int N, int rho,
   }
   __syncthreads();
   const int half = DE / 2;
-  __shared__ float red[NL_THREADS];
+  __shared__ float red[EIG_THREADS];
   __shared__ float off_prev;
   for (int sweep = 0; sweep < 40; ++sweep) {
     // off-diagonal and diagonal squared norms: stop at float32 rounding level
     // (off <= 2^-23 dia), or once a sweep no longer halves off (stagnation:
     // the rotations would only move rounding noise around)
     float off = 0.0f, dia = 0.0f;
-    for (int idx = tid; idx < DE * DE; idx += NL_THREADS) {
+    for (int idx = tid; idx < DE * DE; idx += EIG_THREADS) {
       const float v = A[idx] * A[idx];
       if (idx / DE == idx % DE) dia += v; else off += v;
     }
     red[tid] = off;
     __syncthreads();
-    for (int o = NL_THREADS / 2; o > 0; o >>= 1) {
+    for (int o = EIG_THREADS / 2; o > 0; o >>= 1) {
       if (tid < o) red[tid] += red[tid + o];
       __syncthreads();
     }
@@ -478,7 +479,7 @@ nlm_eig_kernel(const double* __restrict__ csum, int n, int m, int N, int rho,
     __syncthreads();
     red[tid] = dia;
     __syncthreads();
-    for (int o = NL_THREADS / 2; o > 0; o >>= 1) {
+    for (int o = EIG_THREADS / 2; o > 0; o >>= 1) {
       if (tid < o) red[tid] += red[tid + o];
       __syncthreads();
     }
@@ -516,7 +517,7 @@ nlm_eig_kernel(const double* __restrict__ csum, int n, int m, int N, int rho,
       }
       __syncthreads();
       // a lane per rotation (pair j), the block's warps over the rows k
-      constexpr int NG = NL_THREADS / 32;
+      constexpr int NG = EIG_THREADS / 32;
       const int lane = tid & 31, grp = tid >> 5;
       for (int j = lane; j < half; j += 32) {   // columns p, q of A J and V J
         const float c = cs[j][0], sn = cs[j][1];
@@ -562,11 +563,11 @@ nlm_eig_kernel(const double* __restrict__ csum, int n, int m, int N, int rho,
     }
   }
   __syncthreads();
-  for (int idx = tid; idx < rho * D; idx += NL_THREADS) {
+  for (int idx = tid; idx < rho * D; idx += EIG_THREADS) {
     const int d = idx / D, a = idx % D;
     basis[idx] = V[a * DE + pp[d]];
   }
-  for (int a = tid; a < D; a += NL_THREADS) pmean[a] = (float)(mu[a] + shift[a / (m * m)]);
+  for (int a = tid; a < D; a += EIG_THREADS) pmean[a] = (float)(mu[a] + shift[a / (m * m)]);
 }
 
 // Projection of every pixel's shifted patch on the rho leading eigenvectors.
@@ -685,7 +686,7 @@ cudaError_t launch_nlm_guide(const float* f, int n, int H, int W, int m, int rho
   e = cudaFuncSetAttribute(nlm_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_eig);
   if (e != cudaSuccess) return e;
   nlm_sum_kernel<<<(NP + D + 127) / 128, 128, 0, st>>>(cov_part, G, NP + D, cov_sum);
-  nlm_eig_kernel<<<1, NL_THREADS, smem_eig, st>>>(cov_sum, n, m, N, rho, mean_part, G, basis,
+  nlm_eig_kernel<<<1, EIG_THREADS, smem_eig, st>>>(cov_sum, n, m, N, rho, mean_part, G, basis,
                                                   pmean, ctrl);
   const size_t smem_p = sizeof(float) * ((size_t)rho * D + D + 1) + (sizeof(long long) + 3 * sizeof(int)) * (size_t)D +
                         16 + sizeof(float) * 8 * (size_t)D;

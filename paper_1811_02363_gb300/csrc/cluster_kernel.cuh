@@ -55,11 +55,6 @@ namespace {
 // SM): the instantiations for guides of few dimensions keep few coordinates
 // per point in registers and run 32 warps per SM; those for many dimensions
 // run fewer, larger threads.  A chunk is CH points, PPT per thread.
-// Lloyd passes: 1 = each thread tests its own points, margins prefetched one
-// chunk ahead; 0 = the points that need the full test compacted per chunk.
-#ifndef HDF_CL_DIRECT
-#define HDF_CL_DIRECT 1
-#endif
 #ifndef HDF_CL_THREADS
 #define HDF_CL_THREADS 256
 #endif
@@ -1314,7 +1309,6 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
         };
       const int nmine = bid < s.nchunks ? (s.nchunks - bid + a.G - 1) / a.G : 0;
       bool resident = false;
-#if HDF_CL_DIRECT
       if constexpr (resident_bytes<RMAX>() > 0) resident = nmine <= RES_CHUNKS;
       if constexpr (resident_bytes<RMAX>() > 0) if (resident) {
         // Each thread tests its own points.  Their margins and sides live in
@@ -1392,7 +1386,6 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
         }
         if (cur >= 0) flush_split(cur);
       }
-#endif
       if (!resident) {
         // compact each chunk's points that need the full test in position
         // order (coalesced coordinate loads where they are dense) and spread

@@ -88,20 +88,28 @@ bwd_final_kernel(const float* __restrict__ f, const GT* __restrict__ p, int guid
   extern __shared__ float dsm[];
   __shared__ double red[BW_THREADS / 32];
   const int K = ctrl[CTRL_K_EFF];
-  float* smu = dsm;                       // K x rho
-  float* spi = smu + K * rho;             // K x K
-  float* sdA = spi + K * K;               // K x K
+  const int KP = (K + 3) & ~3;            // row pitch of A^{-1} and dA: 16-byte rows, zero padded
+  float* spi = dsm;                       // K x KP
+  float* sdA = spi + K * KP;              // K x KP
+  float* smu = sdA + K * KP;              // K x rho
   for (int i = threadIdx.x; i < K * rho; i += blockDim.x) smu[i] = mu[i];
-  for (int i = threadIdx.x; i < K * K; i += blockDim.x) spi[i] = pinv[i];
+  for (int i = threadIdx.x; i < K * KP; i += blockDim.x) {
+    const int k = i / KP, l = i % KP;
+    spi[i] = l < K ? pinv[k * K + l] : 0.0f;
+  }
   __syncthreads();
-  for (int i = threadIdx.x; i < K * K; i += blockDim.x) {
-    const int k = i / K, l = i % K;
-    float d2 = 0.0f;
-    for (int d = 0; d < rho; ++d) {
-      const float t = smu[k * rho + d] - smu[l * rho + d];
-      d2 = fmaf(t, t, d2);
+  for (int i = threadIdx.x; i < K * KP; i += blockDim.x) {
+    const int k = i / KP, l = i % KP;
+    float v = 0.0f;
+    if (l < K) {
+      float d2 = 0.0f;
+      for (int d = 0; d < rho; ++d) {
+        const float t = smu[k * rho + d] - smu[l * rho + d];
+        d2 = fmaf(t, t, d2);
+      }
+      v = expf(-0.5f * d2 * inv_sr2) * d2 * inv_sr2;     // dA_kl / dlog sigma_r
     }
-    sdA[i] = expf(-0.5f * d2 * inv_sr2) * d2 * inv_sr2;     // dA_kl / dlog sigma_r
+    sdA[i] = v;
   }
   if (threadIdx.x == 0 && blockIdx.x == 0 && ctrl[CTRL_RANKDEF]) record_error(ctrl, HDF_EDOMAIN);
   __syncthreads();
@@ -139,11 +147,20 @@ bwd_final_kernel(const float* __restrict__ f, const GT* __restrict__ p, int guid
         if (k >= K) break;
         float eta = 0.0f, dAc = 0.0f;
         if (!fb) {
+          const float4* pr = reinterpret_cast<const float4*>(spi + k * KP);
+          const float4* dr = reinterpret_cast<const float4*>(sdA + k * KP);
 #pragma unroll
-          for (int l = 0; l < KMAX; ++l) {
-            if (l < K) {
-              eta = fmaf(spi[k * K + l], gv[l], eta);
-              dAc = fmaf(sdA[k * K + l], cv[l], dAc);
+          for (int q = 0; q < KMAX / 4; ++q) {
+            if (4 * q < K) {   // padded entries are 0, and gv, cv are 0 beyond K
+              const float4 pa = pr[q], da = dr[q];
+              eta = fmaf(pa.x, gv[4 * q], eta);
+              eta = fmaf(pa.y, gv[4 * q + 1], eta);
+              eta = fmaf(pa.z, gv[4 * q + 2], eta);
+              eta = fmaf(pa.w, gv[4 * q + 3], eta);
+              dAc = fmaf(da.x, cv[4 * q], dAc);
+              dAc = fmaf(da.y, cv[4 * q + 1], dAc);
+              dAc = fmaf(da.z, cv[4 * q + 2], dAc);
+              dAc = fmaf(da.w, cv[4 * q + 3], dAc);
             }
           }
         }
@@ -206,7 +223,7 @@ cudaError_t launch_final(hdf_handle* h, const float* f, const void* p, int gi, f
                          int blocks, cudaStream_t st) {
   const hdf_desc& d = h->d;
   const float inv_sr2 = (float)(1.0 / (d.sigma_r * d.sigma_r));
-  const size_t smem = sizeof(float) * ((size_t)d.K * d.rho + 2 * (size_t)d.K * d.K);
+  const size_t smem = sizeof(float) * ((size_t)d.K * d.rho + 2 * (size_t)d.K * ((d.K + 3) & ~3));
   if (d.guide_dtype == HDF_GUIDE_BF16)
     bwd_final_kernel<KMAX, RMAX, __nv_bfloat16><<<blocks, BW_THREADS, smem, st>>>(
         f, (const __nv_bfloat16*)p, gi, h->B, h->C, h->bw_gam, h->bw_bet, h->bw_flag, h->mu,

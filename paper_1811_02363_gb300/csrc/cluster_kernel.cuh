@@ -1316,7 +1316,7 @@ __device__ void cluster_run(const ClArgs& a, ClShared& s, unsigned char* dyn) {
         // test reads no global memory; the points that fail it are taken in
         // batches of HB from groups of up to 4 chunks of one split, their
         // coordinates loaded together (one round trip per batch).
-        constexpr int HB = 4;
+        constexpr int HB = RMAX <= 4 ? 4 : 2;
         unsigned short* rmarg = (unsigned short*)(dyn + dyn_stage_offset(rho));
         unsigned char* rside = (unsigned char*)(rmarg + (size_t)RES_CHUNKS * CH);
         int cur = -1, sg = 0;

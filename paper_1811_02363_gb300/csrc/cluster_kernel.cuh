@@ -66,8 +66,8 @@ static_assert(PPT * CL_THREADS == CH && PPT >= 1, "a chunk is a whole number of 
 // Points whose coordinates one thread loads together (registers permitting).
 template <int RMAX>
 __host__ __device__ constexpr int load_batch() {
-  return (RMAX <= 4 ? 8 : (RMAX <= 8 ? 4 : (RMAX <= 16 ? 2 : 1))) < PPT
-             ? (RMAX <= 4 ? 8 : (RMAX <= 8 ? 4 : (RMAX <= 16 ? 2 : 1)))
+  return (RMAX <= 4 ? 8 : (RMAX <= 16 ? 2 : 1)) < PPT
+             ? (RMAX <= 4 ? 8 : (RMAX <= 16 ? 2 : 1))
              : PPT;
 }
 
